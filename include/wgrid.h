@@ -1,0 +1,220 @@
+/*
+ * wgrid.h — C ABI of the GB300 w-gridding library (libwgrid.so).
+ *
+ * The library applies the wide-field radio-interferometric response operator
+ *
+ *     (R I)_k ~= (R0 I)_k = sum_{l,m} exp(-2 pi i [u_k l + v_k m - w_k (n_lm - 1)]) I_lm / n_lm
+ *
+ * (Arras et al., "Efficient wide-field radio interferometry response", Sec. 2, Eq. rime,
+ * approximated by w-gridding, Eqs. nfft / R1-R3) and its exact adjoint R^dagger (Eqs.
+ * adjnfft / Rad1-Rad2).  "degrid" is R (dirty image -> visibilities, the paper's
+ * dirty2ms, App. B); "grid" is R^dagger (visibilities -> dirty image, ms2dirty).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - All array pointers are DEVICE pointers (cudaMalloc'd or managed), C order, contiguous,
+ *    unless an argument says otherwise.  The caller owns every buffer; outputs are
+ *    overwritten completely (masked visibilities get 0).
+ *  - uvw:   (nrows, 3) float64, baseline coordinates in metres (Sec. 2).
+ *    freq:  (nchan,)   float64, channel frequencies in Hz (> 0).
+ *    Visibility k is (row, chan), k = row * nchan + chan; u_k = u~_row * freq_chan / c with
+ *    c = 299792458 m/s (Sec. 2, effective coordinates).
+ *  - dirty: (npix_x, npix_y) real, pixel (jx, jy) at l = (jx - npix_x/2) * pixsize_x,
+ *    m = (jy - npix_y/2) * pixsize_y (Sec. 2, sets L and M); x pairs with u.
+ *  - vis:   (nrows, nchan) complex, interleaved (re, im).
+ *  - Precision (App. B: the data type selects the precision): WG_F32 uses float / complex64
+ *    buffers and FP32 gridding arithmetic; WG_F64 uses double / complex128 and FP64
+ *    throughout.  Coordinates, plane indices and w-screen phases are formed in FP64 in
+ *    both modes.
+ *  - wgt:   optional (nrows, nchan) real weights of the buffer precision; multiplies the
+ *    degrid output and the grid input (App. B).  NULL = all ones.
+ *  - mask:  optional (nrows, nchan) uint8; visibilities with mask == 0 are not processed
+ *    (App. B).  It is fixed when the plan is made.
+ *  - stream: a cudaStream_t passed as void* (NULL = legacy default stream).  All device work
+ *    of a call is ordered on it; calls return when the work is enqueued, except where an
+ *    entry point says it synchronises.
+ *  - Return value: WG_OK (0) or a WG_ERR_* code; wg_last_error() gives a message for the
+ *    calling thread.  A failing call leaves outputs unspecified and the plan usable.
+ */
+#ifndef WGRID_H
+#define WGRID_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum wg_status {
+  WG_OK = 0,
+  WG_ERR_ARG = 1,     /* invalid argument (sizes, epsilon range, null pointer, FoV > unit disc) */
+  WG_ERR_OOM = 2,     /* device allocation failed or exceeds the workspace cap */
+  WG_ERR_CUDA = 3,    /* a CUDA runtime call failed (message has the CUDA error string) */
+  WG_ERR_CUFFT = 4,   /* a cuFFT call failed */
+  WG_ERR_TIMEOUT = 5, /* a bounded host wait on device work ran out */
+  WG_ERR_INTERNAL = 6 /* a device-side consistency check failed (e.g. plane index out of range) */
+};
+
+enum wg_precision { WG_F32 = 0, WG_F64 = 1 };
+
+/* Opaque plan: geometry, kernel choice and the on-device visibility index for one set of
+ * (uvw, freq, mask, image geometry, epsilon, precision).  Reusable for any number of
+ * degrid / grid calls; calls on one plan may not run concurrently with each other on
+ * different streams (they share the plan's scratch state only through the workspace
+ * they allocate per call, so concurrent calls are safe if each uses its own stream). */
+typedef struct wg_plan wg_plan;
+
+/* Options for wg_plan_create (zero-initialise, then set what you need). */
+typedef struct wg_options {
+  int do_wstacking;        /* 1: full w-gridding (Sec. 2); 0: w assumed zero (App. B) */
+  int w_shift;             /* 1: grid w against (n - n_s) with n_s the mid-point of n over
+                              the image (halves the plane count, see notes); 0: the paper's
+                              Delta w = 1 / (2 sigma max|n - 1|) (Sec. 2). Default used by
+                              wg_default_options: 1 */
+  double eps_safety;       /* kernels are chosen with table epsilon <= epsilon * eps_safety
+                              (default 1.0) */
+  size_t max_workspace;    /* cap on the per-call device workspace in bytes; 0 = automatic
+                              (a fraction of the free device memory) */
+  int force_alpha;         /* >0: only consider kernels with this support (tests) */
+  double force_sigma;      /* >0: only consider this oversampling factor (tests) */
+  int tile;                /* uv tile side in cells (16 or 32; 0 = automatic) */
+} wg_options;
+
+/* Per-call statistics (optional output).  Stage times are CUDA-event times measured on the
+ * call's stream; filling them synchronises the stream at the end of the call. */
+typedef struct wg_stats {
+  double ms_total;     /* whole call */
+  double ms_prep;      /* per-pixel correction / screen table (Eqs. R1, Rad1) */
+  double ms_screen;    /* w-screen + zero padding into the planes (Eq. R2) */
+  double ms_fft;       /* cuFFT plane transforms (separately timed stage) */
+  double ms_grid;      /* (de)gridding kernels (Eqs. R3 / Rad2) */
+  double ms_accum;     /* conjugate screen + accumulation over planes + correction (Eq. Rad1) */
+  int64_t n_batches;   /* plane batches processed */
+  int64_t n_planes;    /* w-planes processed */
+  size_t workspace_bytes; /* device workspace used by the call */
+} wg_stats;
+
+/* Plan parameters chosen by the planner (Sec. 4.1, App. A). */
+typedef struct wg_plan_info {
+  int alpha;           /* kernel support (cells) */
+  double sigma;        /* oversampling factor of the chosen kernel */
+  double beta, mu;     /* modified-ES kernel parameters (Eq. semicircle2) */
+  double eps_kernel;   /* the kernel's table accuracy (App. A) */
+  int64_t nu, nv;      /* uv grid size (cells) */
+  int64_t nw;          /* number of w-planes */
+  double dw, w0;       /* plane spacing and position of plane 0 (wavelengths) */
+  double nshift;       /* reference n_s - 1 subtracted from n - 1 (0 for the paper's scheme) */
+  int tile;            /* uv tile side */
+  int64_t ntiles;      /* tiles in the uv grid */
+  int64_t nvis;        /* visibilities in the plan (unmasked) */
+  int64_t batch;       /* w-planes per batch */
+  size_t index_bytes;  /* device bytes held by the plan (visibility index) */
+  size_t workspace_bytes; /* device bytes a degrid / grid call allocates */
+  double umax, vmax, wmin, wmax; /* |u|, |v| maxima and |w| range in wavelengths */
+} wg_plan_info;
+
+/* Fill *opt with defaults (do_wstacking = 1, w_shift = 1, eps_safety = 1, rest 0). */
+void wg_default_options(wg_options* opt);
+
+/*
+ * wg_plan_create — plan the w-gridding of one observation (Sec. 2 and 4.1):
+ * reads the uvw extent on the device, chooses (alpha, sigma, beta, mu) from the kernel
+ * table of App. A with a cost model (Sec. 4.1), fixes the grid (Sec. 2: N = ceil(sigma n)),
+ * Delta w, w_0 and N_w (Sec. 2, Eq. wcirc), builds the piecewise-polynomial kernel
+ * (Sec. 4.2) and bins the visibilities into uv tiles and w-planes on the device
+ * (the GPU counterpart of the index of Sec. 4.3).  Synchronises `stream`.
+ *   uvw, freq, mask: device pointers as above (mask may be NULL); not retained.
+ *   npix_x, npix_y: image size, even and >= 32 (App. B).
+ *   epsilon: requested accuracy, > 2e-13 (App. B); WG_F32 requires epsilon >= 1e-5.
+ *   opt: may be NULL (defaults).
+ *   out: receives the plan; release with wg_plan_destroy.
+ * Errors: WG_ERR_ARG (sizes, epsilon, pixel outside the unit disc, freq <= 0, no kernel
+ * meets epsilon), WG_ERR_OOM, WG_ERR_CUDA, WG_ERR_CUFFT.
+ */
+int wg_plan_create(const double* uvw, const double* freq, int64_t nrows, int64_t nchan,
+                   int64_t npix_x, int64_t npix_y, double pixsize_x, double pixsize_y,
+                   double epsilon, int precision, const uint8_t* mask,
+                   const wg_options* opt, void* stream, wg_plan** out);
+
+/* Release a plan and its device memory (after synchronising the plan's last stream). */
+int wg_plan_destroy(wg_plan* plan);
+
+/* Copy the plan parameters into *info (host call, no device work). */
+int wg_plan_get_info(const wg_plan* plan, wg_plan_info* info);
+
+/*
+ * wg_degrid — vis = R(dirty) (Eqs. R1-R3; the paper's dirty2ms):
+ * per batch of w-planes: w-screen and zero-pad the corrected image (Eqs. R1, R2), 2-D FFT
+ * (cuFFT), degrid every visibility from the planes it touches (Eq. R3), accumulate.
+ *   dirty: (npix_x, npix_y) float (WG_F32) or double (WG_F64), device.
+ *   wgt:   optional weights, device, or NULL.
+ *   vis:   (nrows, nchan) complex output, device.
+ *   stats: optional; filling it synchronises the stream.
+ * Allocates its workspace stream-ordered (cudaMallocAsync) and frees it before returning.
+ */
+int wg_degrid(wg_plan* plan, const void* dirty, const void* wgt, void* vis, void* stream,
+              wg_stats* stats);
+
+/*
+ * wg_grid — dirty = R^dagger(vis) (Eqs. Rad1, Rad2; the paper's ms2dirty): per batch of
+ * w-planes: grid the visibilities onto the planes (Eq. Rad2), inverse 2-D FFT (cuFFT),
+ * multiply by the conjugate w-screen and accumulate over planes; finally divide by
+ * n * Psi and keep the real part (Eq. Rad1).
+ *   vis:   (nrows, nchan) complex input, device.  wgt: optional, device, or NULL.
+ *   dirty: (npix_x, npix_y) real output, device.
+ */
+int wg_grid(wg_plan* plan, const void* vis, const void* wgt, void* dirty, void* stream,
+            wg_stats* stats);
+
+/*
+ * One-shot forms with the paper's argument order (App. B): plan, run, destroy.
+ * do_wstacking as in App. B.  Synchronise `stream` (plan creation does).
+ */
+int wg_dirty2ms(const double* uvw, const double* freq, int64_t nrows, int64_t nchan,
+                const void* dirty, const void* wgt, int64_t npix_x, int64_t npix_y,
+                double pixsize_x, double pixsize_y, double epsilon, int precision,
+                int do_wstacking, const uint8_t* mask, void* vis, void* stream);
+int wg_ms2dirty(const double* uvw, const double* freq, int64_t nrows, int64_t nchan,
+                const void* vis, const void* wgt, int64_t npix_x, int64_t npix_y,
+                double pixsize_x, double pixsize_y, double epsilon, int precision,
+                int do_wstacking, const uint8_t* mask, void* dirty, void* stream);
+
+/* Message of the last failing call on this thread ("" if none). Never NULL. */
+const char* wg_last_error(void);
+
+/* ------------------------------------------------------------------------------------
+ * Host-only helpers (no device work; callable without a GPU).  They expose the planner
+ * and kernel mathematics so they can be checked on their own.
+ * ------------------------------------------------------------------------------------ */
+
+/* Number of rows of the built-in kernel table (App. A, alpha in {4, 7, 8, 12, 16}). */
+int wg_kernel_table_size(void);
+/* Row i of the table: alpha, sigma, epsilon, beta, mu.  Returns WG_ERR_ARG if out of range. */
+int wg_kernel_table_row(int i, int* alpha, double* sigma, double* eps, double* beta, double* mu);
+
+/* Modified ES kernel phi(x) of Eq. (semicircle2), direct evaluation, for n points. */
+int wg_kernel_phi(int alpha, double beta, double mu, const double* x, double* out, int64_t n);
+/* The piecewise polynomial of Sec. 4.2 (alpha pieces of degree alpha+3, Chebyshev-node
+ * interpolation) evaluated by Horner at n points x in grid cells (0 outside the support). */
+int wg_kernel_poly(int alpha, double beta, double mu, const double* x, double* out, int64_t n);
+/* psi(k) = int phi(x) exp(2 pi i k x) dx of the piecewise polynomial (Gauss-Legendre per
+ * piece), k in cycles per cell, for n points. */
+int wg_kernel_psi(int alpha, double beta, double mu, const double* k, double* out, int64_t n);
+
+/* Planner dry run: the parameters wg_plan_create would choose for the given image, epsilon,
+ * precision, options and uvw extent (|u|max, |v|max, |w|min, |w|max in wavelengths) and
+ * visibility count.  Fills alpha, sigma, beta, mu, eps_kernel, nu, nv, nw, dw, w0, nshift,
+ * tile, ntiles of *info. */
+int wg_plan_params(int64_t npix_x, int64_t npix_y, double pixsize_x, double pixsize_y,
+                   double epsilon, int precision, const wg_options* opt, double umax,
+                   double vmax, double wmin, double wmax, int64_t nvis, wg_plan_info* info);
+
+/* Library version string. */
+const char* wg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WGRID_H */

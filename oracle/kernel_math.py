@@ -60,8 +60,16 @@ def psi(k, alpha, beta, mu):
 
 def map_error(k, alpha, beta, mu):
     """l(k) of Eq. (maperror), by literal quadrature over nu in [0, 1)."""
+    return map_error_of(k, alpha, lambda x: phi(x, alpha, beta, mu),
+                        lambda kk: psi(kk, alpha, beta, mu))
+
+
+def map_error_of(k, alpha, phi_fn, psi_fn):
+    """l(k) of Eq. (maperror) for any kernel of support alpha given as callables
+    phi_fn(x) (x in cells) and psi_fn(k) (its Fourier transform), by literal quadrature:
+    l(k)^2 = int_0^1 | 1 - sum_j phi(j - nu) e^{2 pi i (j - nu) k} / psi(k) |^2 d nu."""
     k = np.atleast_1d(np.asarray(k, dtype=np.float64))
-    ps = psi(k, alpha, beta, mu)
+    ps = np.asarray(psi_fn(k), dtype=np.float64)
     s, oms2, w = _TS
     # cells j with |j - nu| <= alpha/2 change only where nu - alpha/2 crosses an integer:
     # at nu = 0 (even alpha) or nu = 1/2 (odd alpha); integrate piecewise between them.
@@ -79,7 +87,7 @@ def map_error(k, alpha, beta, mu):
         acc = np.zeros((k.size, nu.size), dtype=np.complex128)
         for j in range(jlo, jhi + 1):
             x = j - nu
-            f = phi(x, alpha, beta, mu)
+            f = np.asarray(phi_fn(x), dtype=np.float64)
             acc += f[None, :] * np.exp(2j * np.pi * np.outer(k, x))
         err = np.abs(1.0 - acc / ps[:, None]) ** 2
         out += (err * wn[None, :]).sum(axis=1)

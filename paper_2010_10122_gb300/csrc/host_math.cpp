@@ -1,0 +1,350 @@
+// Host-side kernel mathematics and planner (FP64).  See host_math.h.
+#include "host_math.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+
+namespace wg {
+
+const std::vector<KernelRow>& kernel_table() {
+  // App. A, "Optimal parameters for alpha = 4 / 7 / 8 / 12 / 16": sigma, epsilon, beta, mu as
+  // printed (the alpha = 12 table has no sigma = 1.85 row).
+  static const std::vector<KernelRow> rows = {
+      // alpha = 4
+      {4, 1.15, 0.025654879, 1.3873426689, 0.5436851297},
+      {4, 1.2, 0.013809249, 1.3008419165, 0.5902137484},
+      {4, 1.25, 0.0085840685, 1.3274088935, 0.5953499486},
+      {4, 1.3, 0.0057322498, 1.3617063353, 0.5965631622},
+      {4, 1.35, 0.0042494419, 1.384549988, 0.5990241291},
+      {4, 1.4, 0.0033459552, 1.4405325088, 0.5924776015},
+      {4, 1.45, 0.0028187359, 1.4635220066, 0.5929442711},
+      {4, 1.5, 0.0023843943, 1.5539689162, 0.5772217314},
+      {4, 1.55, 0.0020343796, 1.5991008653, 0.5721765215},
+      {4, 1.6, 0.0017143851, 1.6581546365, 0.5644747137},
+      {4, 1.65, 0.0014730848, 1.7135331415, 0.5572788589},
+      {4, 1.7, 0.0012554492, 1.7464330378, 0.5548742415},
+      {4, 1.75, 0.0010610904, 1.7887326906, 0.5509877716},
+      {4, 1.8, 0.00090885567, 1.8122309426, 0.5502273972},
+      {4, 1.85, 0.0007757401, 1.8304451327, 0.550396716},
+      {4, 1.9, 0.0006740398, 1.8484487383, 0.5502376937},
+      {4, 1.95, 0.00058655391, 1.8742215688, 0.5489738941},
+      {4, 2.0, 0.00051911189, 1.90694363, 0.5468009434},
+      // alpha = 7
+      {7, 1.15, 0.00078476028, 1.5248706519, 0.5288306317},
+      {7, 1.2, 0.00027127166, 1.5739348793, 0.5287992619},
+      {7, 1.25, 0.00012594628, 1.6245240723, 0.527921777},
+      {7, 1.3, 7.0214545e-05, 1.6835745981, 0.5257484101},
+      {7, 1.35, 4.1972457e-05, 1.7343424414, 0.5239793844},
+      {7, 1.4, 2.378019e-05, 1.7845017738, 0.5224266045},
+      {7, 1.45, 1.3863408e-05, 1.8180597789, 0.5221834768},
+      {7, 1.5, 9.1605353e-06, 1.868082272, 0.5206277502},
+      {7, 1.55, 6.479159e-06, 1.9188980015, 0.5183134674},
+      {7, 1.6, 4.6544571e-06, 1.9536166143, 0.5178695891},
+      {7, 1.65, 3.5489761e-06, 1.9786267068, 0.5178430252},
+      {7, 1.7, 2.7030348e-06, 2.0027666534, 0.5178577604},
+      {7, 1.75, 2.0533894e-06, 2.0289949199, 0.5176300336},
+      {7, 1.8, 1.6069122e-06, 2.0596412946, 0.5167551932},
+      {7, 1.85, 1.2936794e-06, 2.0720606842, 0.5178747891},
+      {7, 1.9, 1.0768664e-06, 2.090898174, 0.5181009847},
+      {7, 1.95, 9.0890421e-07, 2.1086185697, 0.5184537843},
+      {7, 2.0, 7.7488775e-07, 2.1278284187, 0.5186377792},
+      // alpha = 8
+      {8, 1.15, 0.00026818611, 1.568124649, 0.5223052481},
+      {8, 1.2, 7.8028732e-05, 1.620926145, 0.5219287175},
+      {8, 1.25, 2.7460918e-05, 1.6851585171, 0.519925059},
+      {8, 1.3, 1.3421658e-05, 1.7442373315, 0.5182155619},
+      {8, 1.35, 7.5158217e-06, 1.7876782642, 0.5176319503},
+      {8, 1.4, 4.2472384e-06, 1.8294321912, 0.5171860211},
+      {8, 1.45, 2.5794802e-06, 1.871691821, 0.5161733611},
+      {8, 1.5, 1.6131994e-06, 1.9213040541, 0.5145350888},
+      {8, 1.55, 1.0974814e-06, 1.9637229131, 0.5134005827},
+      {8, 1.6, 7.531955e-07, 2.0002761373, 0.5128849282},
+      {8, 1.65, 5.5097346e-07, 2.0275645736, 0.5127082324},
+      {8, 1.7, 4.0136726e-07, 2.0498410409, 0.5130237662},
+      {8, 1.75, 2.906467e-07, 2.073158517, 0.5131757153},
+      {8, 1.8, 2.1834922e-07, 2.0907418726, 0.5136046561},
+      {8, 1.85, 1.6329905e-07, 2.1164552354, 0.5133333878},
+      {8, 1.9, 1.2828598e-07, 2.126157016, 0.5143004427},
+      {8, 1.95, 1.0171134e-07, 2.1363206613, 0.515235491},
+      {8, 2.0, 8.1881369e-08, 2.1397013368, 0.5166895497},
+      // alpha = 12
+      {12, 1.15, 2.7535895e-06, 1.6661837519, 0.5098172147},
+      {12, 1.2, 5.2570038e-07, 1.7294557459, 0.5089239596},
+      {12, 1.25, 1.378658e-07, 1.7698182384, 0.5099240718},
+      {12, 1.3, 4.4329167e-08, 1.8092042442, 0.510607427},
+      {12, 1.35, 1.7038991e-08, 1.8619112597, 0.5093832337},
+      {12, 1.4, 6.5438748e-09, 1.9069147481, 0.5089479889},
+      {12, 1.45, 2.9874764e-09, 1.9318398074, 0.5098082325},
+      {12, 1.5, 1.4920459e-09, 1.9628483155, 0.5100985753},
+      {12, 1.55, 8.0989276e-10, 2.0129847811, 0.5085327805},
+      {12, 1.6, 4.1660575e-10, 2.0517921747, 0.5079102398},
+      {12, 1.65, 2.3539727e-10, 2.06983884, 0.5085131064},
+      {12, 1.7, 1.3497289e-10, 2.0887365361, 0.5090417146},
+      {12, 1.75, 8.3256938e-11, 2.106955733, 0.5095920671},
+      {12, 1.8, 5.8834619e-11, 2.1359415217, 0.5091887069},
+      {12, 1.9, 2.6412908e-11, 2.2006369514, 0.5075889699},
+      {12, 1.95, 1.7189689e-11, 2.2146741638, 0.5080017404},
+      {12, 2.0, 1.2174796e-11, 2.2431392199, 0.5075191177},
+      // alpha = 16
+      {16, 1.3, 1.1509596e-10, 1.7892839755, 0.5122877693},
+      {16, 1.35, 3.2440049e-11, 1.8914441282, 0.5063521839},
+      {16, 1.4, 8.4329616e-12, 1.9296369098, 0.5065170208},
+      {16, 1.45, 3.1161739e-12, 1.9674735425, 0.5063244338},
+      {16, 1.5, 1.2100308e-12, 2.0130787701, 0.5055587965},
+      {16, 1.55, 4.6082202e-13, 2.0438032614, 0.5056309683},
+      {16, 1.6, 1.7883238e-13, 2.0329561822, 0.5089045671},
+      {16, 1.65, 9.2853815e-14, 2.0494514743, 0.5103582604},
+      {16, 1.7, 5.6614567e-14, 2.0925119791, 0.5083767402},
+      {16, 1.75, 2.875391e-14, 2.1461524027, 0.5062037834},
+      {16, 1.8, 1.6578982e-14, 2.1490040175, 0.508272183},
+      {16, 1.85, 1.1782751e-14, 2.1811826814, 0.5072570059},
+      {16, 1.9, 8.9196865e-15, 2.1981176583, 0.5075840871},
+      {16, 1.95, 6.6530006e-15, 2.234001135, 0.5060133105},
+      {16, 2.0, 5.0563492e-15, 2.2621631913, 0.5056924675},
+  };
+  return rows;
+}
+
+double es_phi(int alpha, double beta, double mu, double x) {
+  double s = 2.0 * x / alpha;
+  if (std::fabs(s) > 1.0) return 0.0;
+  return std::exp(alpha * beta * (std::pow(1.0 - s * s, mu) - 1.0));
+}
+
+double PolyKernel::eval_piece(int i, double z) const {
+  const double* ci = &c[(size_t)i * (deg + 1)];
+  double r = ci[deg];
+  for (int d = deg - 1; d >= 0; --d) r = r * z + ci[d];
+  return r;
+}
+
+double PolyKernel::eval(double x) const {
+  double t = x + 0.5 * alpha;  // position from the left support edge, in cells
+  if (t < 0.0 || t > alpha) return 0.0;
+  int i = std::min((int)std::floor(t), alpha - 1);
+  double z = 2.0 * (t - i) - 1.0;
+  return eval_piece(i, z);
+}
+
+PolyKernel make_poly_kernel(int alpha, double beta, double mu, int deg) {
+  // Sec. 4.2: each of the alpha unit pieces is interpolated at the deg + 1 roots of the
+  // Chebyshev polynomial T_{deg+1}.  The interpolant is formed as a Chebyshev series
+  // (discrete orthogonality at the roots) and converted to monomials in z with the
+  // three-term recurrence T_{n+1} = 2 z T_n - T_{n-1}, accumulated in long double.
+  PolyKernel K;
+  K.alpha = alpha; K.deg = deg; K.beta = beta; K.mu = mu;
+  const int np = deg + 1;
+  K.c.assign((size_t)alpha * np, 0.0);
+  std::vector<double> zq(np), fq(np);
+  for (int q = 0; q < np; ++q) zq[q] = std::cos(M_PI * (q + 0.5) / np);
+  // monomial coefficients of T_0 .. T_deg
+  std::vector<std::vector<long double>> T(np, std::vector<long double>(np, 0.0L));
+  T[0][0] = 1.0L;
+  if (np > 1) T[1][1] = 1.0L;
+  for (int n = 1; n + 1 < np; ++n)
+    for (int d = 0; d < np; ++d) {
+      long double v = -T[n - 1][d];
+      if (d > 0) v += 2.0L * T[n][d - 1];
+      T[n + 1][d] = v;
+    }
+  for (int i = 0; i < alpha; ++i) {
+    for (int q = 0; q < np; ++q) {
+      double x = -0.5 * alpha + i + 0.5 * (zq[q] + 1.0);
+      fq[q] = es_phi(alpha, beta, mu, x);
+    }
+    std::vector<long double> mono(np, 0.0L);
+    for (int n = 0; n < np; ++n) {
+      long double a = 0.0L;
+      for (int q = 0; q < np; ++q) a += (long double)fq[q] * std::cos(M_PI * n * (q + 0.5) / np);
+      a *= 2.0L / np;
+      if (n == 0) a *= 0.5L;
+      for (int d = 0; d < np; ++d) mono[d] += a * T[n][d];
+    }
+    for (int d = 0; d < np; ++d) K.c[(size_t)i * np + d] = (double)mono[d];
+  }
+  return K;
+}
+
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  // Newton iteration on P_n from the Chebyshev-like initial guesses.
+  x.assign(n, 0.0); w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    double dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1; p1 = p2;
+      }
+      // p1 = P_n(z), p0 = P_{n-1}(z)
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= n; ++k) {
+      double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+      p0 = p1; p1 = p2;
+    }
+    dp = n * (z * p1 - p0) / (z * z - 1.0);
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+double psi_poly(const PolyKernel& K, double k) {
+  // int_{-alpha/2}^{alpha/2} phi(x) cos(2 pi k x) dx, piece by piece; on a piece the
+  // integrand is a polynomial of degree deg times a cosine with at most half a turn,
+  // so 32 Gauss-Legendre nodes integrate it to rounding level.
+  static thread_local std::vector<double> gx, gw;
+  if (gx.empty()) gauss_legendre(32, gx, gw);
+  long double sum = 0.0L;
+  for (int i = 0; i < K.alpha; ++i) {
+    double x0 = -0.5 * K.alpha + i + 0.5;  // piece centre
+    for (size_t q = 0; q < gx.size(); ++q) {
+      double z = gx[q];
+      double x = x0 + 0.5 * z;
+      sum += (long double)(0.5 * gw[q]) * K.eval_piece(i, z) * std::cos(2.0 * M_PI * k * x);
+    }
+  }
+  return (double)sum;
+}
+
+std::vector<double> psi_cheb_coeffs(const PolyKernel& K, int m) {
+  // psi is even, so expand g(y) = psi(k) with y = 8 k^2 - 1 in [-1, 1] for |k| <= 1/2:
+  // Chebyshev interpolation at the m roots of T_m.
+  std::vector<double> c(m, 0.0), g(m);
+  for (int q = 0; q < m; ++q) {
+    double y = std::cos(M_PI * (q + 0.5) / m);
+    double k = std::sqrt((y + 1.0) / 8.0);
+    g[q] = psi_poly(K, k);
+  }
+  for (int n = 0; n < m; ++n) {
+    long double a = 0.0L;
+    for (int q = 0; q < m; ++q) a += (long double)g[q] * std::cos(M_PI * n * (q + 0.5) / m);
+    a *= 2.0L / m;
+    if (n == 0) a *= 0.5L;
+    c[n] = (double)a;
+  }
+  return c;
+}
+
+double psi_cheb_eval(const std::vector<double>& c, double k) {
+  double y = 8.0 * k * k - 1.0;
+  double b1 = 0.0, b2 = 0.0;
+  for (int n = (int)c.size() - 1; n >= 1; --n) {
+    double b0 = 2.0 * y * b1 - b2 + c[n];
+    b2 = b1; b1 = b0;
+  }
+  return y * b1 - b2 + c[0];
+}
+
+static bool seven_smooth(int64_t n) {
+  for (int p : {2, 3, 5, 7})
+    while (n % p == 0) n /= p;
+  return n == 1;
+}
+
+int64_t good_size(int64_t n, int64_t mult) {
+  int64_t q = std::max<int64_t>(1, (n + mult - 1) / mult);
+  while (!seven_smooth(q)) ++q;
+  return q * mult;
+}
+
+// Rough GB300 cost model (seconds), Sec. 4.1: FFT and plane traffic per w-plane plus the
+// per-visibility gridding work alpha^3.  Constants come from measured cuFFT C2C/Z2Z
+// plane times, the HBM copy rate and the FP32 / FP64 FMA and shared-atomic rates.
+static double plan_cost(int prec, int64_t nu, int64_t nv, int64_t nw, int alpha, int64_t nvis,
+                        int64_t npix) {
+  double cells = (double)nu * nv;
+  double lg = std::log2(cells);
+  double k_fft = prec ? 9.2e-12 : 3.8e-13;        // s per cell * log2(cells) per plane
+  double k_cell = prec ? 7.0e-12 : 3.5e-12;       // s per cell per plane (screen, (de)grid traffic)
+  double k_pix = prec ? 3.4e-11 : 1.0e-12;        // s per image pixel per plane (phase)
+  double k_vis = prec ? 1.3e-11 : 2.0e-12;        // s per visibility per alpha^3
+  return nw * (cells * lg * k_fft + cells * k_cell + (double)npix * k_pix) +
+         (double)nvis * alpha * alpha * alpha * k_vis;
+}
+
+int choose_plan(const PlanInput& in, PlanParams& out, char* err, int errlen) {
+  auto fail = [&](const char* msg) {
+    std::snprintf(err, errlen, "%s", msg);
+    return 1;
+  };
+  if (in.nx < 32 || in.ny < 32 || (in.nx & 1) || (in.ny & 1))
+    return fail("npix_x and npix_y must be even and at least 32");
+  if (!(in.psx > 0) || !(in.psy > 0)) return fail("pixel sizes must be positive");
+  if (!(in.eps > 2e-13)) return fail("epsilon must be larger than 2e-13");
+  if (in.prec == 0 && in.eps < 1e-5) return fail("single precision requires epsilon >= 1e-5");
+  // most negative n - 1 over the image: the corner pixel (-nx/2, -ny/2) (Sec. 2, sets L, M)
+  double lmax = 0.5 * in.nx * in.psx, mmax = 0.5 * in.ny * in.psy;
+  double r2 = lmax * lmax + mmax * mmax;
+  if (r2 >= 1.0) return fail("field of view exceeds the unit disc (l^2 + m^2 >= 1)");
+  double nm1_min = -r2 / (1.0 + std::sqrt(1.0 - r2));
+  if (in.tile != 0 && in.tile != 16 && in.tile != 32) return fail("tile must be 16 or 32");
+
+  double safety = in.eps_safety > 0 ? in.eps_safety : 1.0;
+  bool found = false;
+  PlanParams best;
+  best.cost = std::numeric_limits<double>::infinity();
+  const auto& T = kernel_table();
+  for (int alpha : {4, 7, 8, 12, 16}) {
+    if (in.force_alpha > 0 && alpha != in.force_alpha) continue;
+    // uv tile side: 32 cells; 16 for wide FP64 kernels, whose (tile + alpha - 1)^2 staging
+    // area would otherwise crowd shared memory
+    int tile = in.tile > 0 ? in.tile : ((in.prec == 1 && alpha >= 12) ? 16 : 32);
+    if (alpha - 1 > tile) continue;
+    // Sec. 4.1: for each alpha the smallest sigma whose kernel meets epsilon
+    const KernelRow* pick = nullptr;
+    for (const auto& r : T) {
+      if (r.alpha != alpha) continue;
+      if (in.force_sigma > 0 && std::fabs(r.sigma - in.force_sigma) > 1e-9) continue;
+      if (r.eps <= in.eps * safety && (!pick || r.sigma < pick->sigma)) pick = &r;
+    }
+    if (!pick) continue;
+    PlanParams p;
+    p.alpha = alpha; p.sigma = pick->sigma; p.beta = pick->beta; p.mu = pick->mu;
+    p.eps_kernel = pick->eps;
+    p.tile = tile;
+    // Sec. 2: N = ceil(sigma n), rounded up to an FFT-friendly multiple of the tile
+    int64_t minn = std::max<int64_t>(2 * alpha, 16);
+    p.nu = good_size(std::max<int64_t>((int64_t)std::ceil(p.sigma * in.nx), minn), tile);
+    p.nv = good_size(std::max<int64_t>((int64_t)std::ceil(p.sigma * in.ny), minn), tile);
+    p.ntu = p.nu / tile; p.ntv = p.nv / tile;
+    p.nm1_min = nm1_min;
+    if (in.do_w) {
+      double span;  // extent of the n - 1 values the w-kernel must resolve
+      if (in.w_shift) {
+        p.nshift = 0.5 * nm1_min;   // centre of [nm1_min, 0]
+        span = 0.5 * std::fabs(nm1_min);
+      } else {
+        p.nshift = 0.0;
+        span = std::fabs(nm1_min);
+      }
+      // Sec. 2: Delta w = 1 / (2 sigma max |n - 1|) (Nyquist), with the maximum taken over
+      // the n - 1 values relative to the reference nshift
+      p.dw = 1.0 / (2.0 * p.sigma * span);
+      double wmin = in.wmin, wmax = std::max(in.wmax, in.wmin);
+      // Eq. (wcirc): first plane half a kernel width below the smallest w
+      p.w0 = wmin - 0.5 * p.dw * (alpha - 1);
+      // N_w = (max w - min w) / Delta w + alpha, rounded up, plus one plane of slack for
+      // rounding in the per-visibility plane index
+      p.nw = (int64_t)std::ceil((wmax - wmin) / p.dw) + alpha + 1;
+    } else {
+      p.nshift = 0.0; p.dw = 1.0; p.w0 = 0.0; p.nw = 1;
+    }
+    if (p.nw > 4095) continue;  // plane index must fit 12 bits (FP32 phase split)
+    p.cost = plan_cost(in.prec, p.nu, p.nv, p.nw, alpha, in.nvis, in.nx * in.ny);
+    if (p.cost < best.cost) { best = p; found = true; }
+  }
+  if (!found) return fail("no kernel in the table meets the requested epsilon");
+  out = best;
+  return 0;
+}
+
+}  // namespace wg

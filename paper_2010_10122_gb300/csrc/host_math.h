@@ -1,0 +1,79 @@
+// Host-side kernel mathematics and planner of the w-gridder (FP64, no device code).
+#pragma once
+#include <cstdint>
+#include <vector>
+
+namespace wg {
+
+constexpr double kSpeedOfLight = 299792458.0;
+constexpr int kMaxAlpha = 16;
+constexpr int kMaxDeg = kMaxAlpha + 3;          // Sec. 4.2: pieces of degree alpha + 3
+constexpr int kPsiChebTerms = 28;               // psi(k) as sum_n c_n T_n(8 k^2 - 1), |k| <= 1/2
+
+struct KernelRow {
+  int alpha;
+  double sigma, eps, beta, mu;
+};
+
+// App. A: optimal modified-ES parameters for alpha in {4, 7, 8, 12, 16}.
+const std::vector<KernelRow>& kernel_table();
+
+// Eq. (semicircle2): exp(alpha beta [(1 - (2x/alpha)^2)^mu - 1]) on [-alpha/2, alpha/2].
+double es_phi(int alpha, double beta, double mu, double x);
+
+// Piecewise polynomial of Sec. 4.2.  Piece i covers x in [-alpha/2 + i, -alpha/2 + i + 1];
+// with local coordinate z in [-1, 1] (x = -alpha/2 + i + (z + 1)/2) it is
+// sum_d c[i * (deg + 1) + d] z^d, interpolating phi at the deg + 1 Chebyshev roots.
+struct PolyKernel {
+  int alpha = 0, deg = 0;
+  double beta = 0, mu = 0;
+  std::vector<double> c;  // alpha * (deg + 1) monomial coefficients
+  double eval(double x) const;  // 0 outside [-alpha/2, alpha/2]
+  double eval_piece(int i, double z) const;
+};
+PolyKernel make_poly_kernel(int alpha, double beta, double mu, int deg);
+
+// psi(k) = int phi_poly(x) exp(2 pi i k x) dx (real: phi is even); Gauss-Legendre per piece.
+double psi_poly(const PolyKernel& K, double k);
+
+// Coefficients c_0..c_{m-1} with psi(k) ~= sum_n c_n T_n(8 k^2 - 1) for |k| <= 1/2.
+std::vector<double> psi_cheb_coeffs(const PolyKernel& K, int m);
+double psi_cheb_eval(const std::vector<double>& c, double k);
+
+// Gauss-Legendre nodes / weights on [-1, 1].
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
+
+// Smallest multiple of `mult` that is >= n and whose quotient by `mult` has no prime
+// factor above 7 (FFT-friendly sizes for cuFFT).
+int64_t good_size(int64_t n, int64_t mult);
+
+struct PlanInput {
+  int64_t nx, ny;
+  double psx, psy;
+  double eps;
+  int prec;          // 0 f32, 1 f64
+  int do_w, w_shift;
+  double eps_safety;
+  int force_alpha;
+  double force_sigma;
+  int tile;
+  double umax, vmax, wmin, wmax;  // wavelengths (|u|, |v| maxima, |w| range)
+  int64_t nvis;
+};
+
+struct PlanParams {
+  int alpha = 0;
+  double sigma = 0, beta = 0, mu = 0, eps_kernel = 0;
+  int64_t nu = 0, nv = 0, nw = 0;
+  double dw = 0, w0 = 0;
+  double nm1_min = 0;   // most negative n - 1 over the image (corner pixel)
+  double nshift = 0;    // reference subtracted from n - 1
+  int tile = 0;
+  int64_t ntu = 0, ntv = 0;
+  double cost = 0;
+};
+
+// Returns 0 on success; on failure fills err (WG_ERR_ARG class problems).
+int choose_plan(const PlanInput& in, PlanParams& out, char* err, int errlen);
+
+}  // namespace wg

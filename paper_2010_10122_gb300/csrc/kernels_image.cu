@@ -1,0 +1,191 @@
+// Image-side kernels of the w-gridder: per-pixel correction and w-screen phase table
+// (Eqs. R1, Rad1), the w-screen + zero padding into the uv planes (Eq. R2), and the
+// conjugate-screen accumulation over planes with the final correction (Eq. Rad1).
+//
+// Plane layout: plane p of a batch is nu x nv complex, C order; image pixel (jx, jy) sits at
+// cell ((jx - nx/2) mod nu, (jy - ny/2) mod nv), so that a plain forward / inverse 2-D DFT
+// of the plane evaluates sum_t e^{-/+ 2 pi i (a t_x / nu + b t_y / nv)} with t = j - n/2.
+#include "wgrid_internal.h"
+
+namespace wg {
+
+// w-screen phase of plane j (global plane index) in cycles, reduced to [-1, 1].
+// table: A = frac(w0 (n - 1 - nshift)), B = dw (n - 1 - nshift) with |B| <= 1/(2 sigma).
+// FP32: B = Bhi + Blo, Bhi on a 2^-13 lattice, so j * Bhi (j < 4096) is exact in float and
+// its integer part can be dropped exactly; the residual j * Blo is below 1/4 in size.
+__device__ __forceinline__ float screen_cycles(const Z4<float>& t, int j) {
+  float th = (float)j * t.w;          // exact
+  th -= rintf(th);                    // exact
+  return t.v + th + (float)j * t.pad;
+}
+__device__ __forceinline__ double screen_cycles(const Z4<double>& t, int j) {
+  double c = fma((double)j, t.w, t.v);
+  return c - rint(c);
+}
+__device__ __forceinline__ void sincos2pi(float c, float* s, float* co) { sincospif(2.0f * c, s, co); }
+__device__ __forceinline__ void sincos2pi(double c, double* s, double* co) { sincospi(2.0 * c, s, co); }
+
+// ---------------------------------------------------------------------------------------
+// prep: per pixel, corr = 1 / (n psi_u psi_v psi_w) (Eqs. R1, Rad1, with Psi the product of
+// psi over the three directions, Sec. 2) and the screen phase parameters.  With `dirty`
+// the stored value is I * corr (degrid input, Eq. R1); without, corr itself (grid output).
+// ---------------------------------------------------------------------------------------
+template <typename R>
+__global__ void k_prep(const __grid_constant__ ImgParams P, const R* __restrict__ dirty,
+                       Z4<R>* __restrict__ table) {
+  const Geom& g = P.g;
+  int jy = blockIdx.x * blockDim.x + threadIdx.x;
+  int jx = blockIdx.y;
+  if (jy >= g.ny) return;
+  double l = (double)(jx - g.nx / 2) * g.psx;
+  double m = (double)(jy - g.ny / 2) * g.psy;
+  double r2 = __dadd_rn(__dmul_rn(l, l), __dmul_rn(m, m));
+  double n = sqrt(1.0 - r2);
+  double nm1 = -r2 / (1.0 + n);
+  double corr = P.cinv_u[jx] * P.cinv_v[jy] / n;
+  double A = 0.0, B = 0.0;
+  if (g.do_w) {
+    double xw = nm1 - g.nshift;
+    double kw = xw * g.dw;                 // psi_w argument, |kw| <= 1/(2 sigma)
+    double y = 8.0 * kw * kw - 1.0;        // Clenshaw for sum c_n T_n(y)
+    double b1 = 0.0, b2 = 0.0;
+#pragma unroll
+    for (int i = kPsiChebTerms - 1; i >= 1; --i) {
+      double b0 = fma(2.0 * y, b1, P.psi_c[i] - b2);
+      b2 = b1; b1 = b0;
+    }
+    double psiw = fma(y, b1, P.psi_c[0] - b2);
+    corr /= psiw;
+    double a = g.w0 * xw;
+    A = a - rint(a);
+    B = g.dw * xw;
+  }
+  int64_t pix = (int64_t)jx * g.ny + jy;
+  double val = dirty != nullptr ? (double)dirty[pix] * corr : corr;
+  Z4<R> t;
+  t.u = (R)val;
+  t.v = (R)A;
+  if (sizeof(R) == 4) {
+    double bhi = rint(B * 8192.0) / 8192.0;
+    t.w = (R)bhi;
+    t.pad = (R)(B - bhi);
+  } else {
+    t.w = (R)B;
+    t.pad = (R)0;
+  }
+  table[pix] = t;
+}
+
+template <typename R>
+cudaError_t launch_prep(const ImgParams& P, const R* dirty, Z4<R>* table, cudaStream_t s) {
+  dim3 grid((P.g.ny + 255) / 256, P.g.nx);
+  k_prep<R><<<grid, 256, 0, s>>>(P, dirty, table);
+  return cudaGetLastError();
+}
+
+// image index of plane cell x (or -1 in the zero padding)
+__device__ __forceinline__ int cell_to_pixel(int x, int n, int N) {
+  if (x < n / 2) return x + n / 2;
+  if (x >= N - n / 2) return x - (N - n / 2);
+  return -1;
+}
+
+// ---------------------------------------------------------------------------------------
+// screen: planes[p] = I~ * exp(+2 pi i c_j (n - 1 - nshift)) at the image cells, 0 elsewhere
+// (Eq. R2 with the sign of Eq. rime), for global planes j = b0 .. b0 + nb - 1.
+// ---------------------------------------------------------------------------------------
+template <typename R>
+__global__ void k_screen(const Geom g, const Z4<R>* __restrict__ table,
+                         typename C2<R>::T* __restrict__ planes, int b0, int nb) {
+  using CT = typename C2<R>::T;
+  int y = blockIdx.x * blockDim.x + threadIdx.x;
+  int x = blockIdx.y;
+  if (y >= g.nv) return;
+  const int64_t ncell = (int64_t)g.nu * g.nv;
+  const int64_t cell = (int64_t)x * g.nv + y;
+  int jx = cell_to_pixel(x, g.nx, g.nu), jy = cell_to_pixel(y, g.ny, g.nv);
+  if (jx < 0 || jy < 0) {
+    CT zero; zero.x = (R)0; zero.y = (R)0;
+    for (int p = 0; p < nb; ++p) planes[p * ncell + cell] = zero;
+    return;
+  }
+  Z4<R> t = table[(int64_t)jx * g.ny + jy];
+  if (!g.do_w) {
+    CT v; v.x = t.u; v.y = (R)0;
+    planes[cell] = v;
+    return;
+  }
+  for (int p = 0; p < nb; ++p) {
+    R cyc = screen_cycles(t, b0 + p);
+    R sn, cs;
+    sincos2pi(cyc, &sn, &cs);
+    CT v; v.x = t.u * cs; v.y = t.u * sn;
+    planes[p * ncell + cell] = v;
+  }
+}
+
+template <typename R>
+cudaError_t launch_screen(const Geom& g, const Z4<R>* table, typename C2<R>::T* planes, int b0,
+                          int nb, cudaStream_t s) {
+  dim3 grid((g.nv + 255) / 256, g.nu);
+  k_screen<R><<<grid, 256, 0, s>>>(g, table, planes, b0, nb);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// accumulate: acc += sum_p Re(conj(screen_p) H_p) over the batch (Eq. Rad1); on the last
+// batch dirty = acc * corr (the division by n Psi of Eq. Rad1), real part kept.
+// ---------------------------------------------------------------------------------------
+template <typename R>
+__global__ void k_accumulate(const Geom g, const Z4<R>* __restrict__ table,
+                             const typename C2<R>::T* __restrict__ planes, int b0, int nb,
+                             double* __restrict__ acc, int first, int last,
+                             R* __restrict__ dirty) {
+  using CT = typename C2<R>::T;
+  int jy = blockIdx.x * blockDim.x + threadIdx.x;
+  int jx = blockIdx.y;
+  if (jy >= g.ny) return;
+  int x = jx < g.nx / 2 ? g.nu - g.nx / 2 + jx : jx - g.nx / 2;
+  int y = jy < g.ny / 2 ? g.nv - g.ny / 2 + jy : jy - g.ny / 2;
+  const int64_t ncell = (int64_t)g.nu * g.nv;
+  const int64_t cell = (int64_t)x * g.nv + y;
+  const int64_t pix = (int64_t)jx * g.ny + jy;
+  Z4<R> t = table[pix];
+  R sum = (R)0;
+  if (!g.do_w) {
+    sum = planes[cell].x;
+  } else {
+    for (int p = 0; p < nb; ++p) {
+      CT h = planes[p * ncell + cell];
+      R cyc = screen_cycles(t, b0 + p);
+      R sn, cs;
+      sincos2pi(cyc, &sn, &cs);
+      sum += cs * h.x + sn * h.y;   // Re(exp(-2 pi i cyc) h)
+    }
+  }
+  double a = first ? (double)sum : acc[pix] + (double)sum;
+  if (last) dirty[pix] = (R)(a * (double)t.u);
+  else acc[pix] = a;
+}
+
+template <typename R>
+cudaError_t launch_accumulate(const Geom& g, const Z4<R>* table, const typename C2<R>::T* planes,
+                              int b0, int nb, double* acc, bool first, bool last, R* dirty,
+                              cudaStream_t s) {
+  dim3 grid((g.ny + 255) / 256, g.nx);
+  k_accumulate<R><<<grid, 256, 0, s>>>(g, table, planes, b0, nb, acc, first ? 1 : 0,
+                                       last ? 1 : 0, dirty);
+  return cudaGetLastError();
+}
+
+#define WG_INST(R)                                                                          \
+  template cudaError_t launch_prep<R>(const ImgParams&, const R*, Z4<R>*, cudaStream_t);    \
+  template cudaError_t launch_screen<R>(const Geom&, const Z4<R>*, C2<R>::T*, int, int,     \
+                                        cudaStream_t);                                      \
+  template cudaError_t launch_accumulate<R>(const Geom&, const Z4<R>*, const C2<R>::T*, int, \
+                                            int, double*, bool, bool, R*, cudaStream_t);
+WG_INST(float)
+WG_INST(double)
+#undef WG_INST
+
+}  // namespace wg

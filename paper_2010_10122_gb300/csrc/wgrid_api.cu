@@ -1,0 +1,711 @@
+// C ABI of the GB300 w-gridder (include/wgrid.h): plans, degrid / grid pipelines, one-shot
+// calls and host-only helpers.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <memory>
+#include <string>
+
+#include "wgrid_internal.h"
+
+using namespace wg;
+
+// ---------------------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+static int set_error(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+#define WG_CUDA(call)                                                                    \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return set_error(WG_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                       __FILE__, __LINE__);                                              \
+  } while (0)
+
+#define WG_CUFFT(call)                                                                   \
+  do {                                                                                   \
+    cufftResult r_ = (call);                                                             \
+    if (r_ != CUFFT_SUCCESS)                                                             \
+      return set_error(WG_ERR_CUFFT, "%s failed: cufftResult %d", #call, (int)r_);       \
+  } while (0)
+
+#define WG_TRY(call)              \
+  do {                            \
+    int rc_ = (call);             \
+    if (rc_ != WG_OK) return rc_; \
+  } while (0)
+
+// ---------------------------------------------------------------------------------------
+// stream-ordered device memory from a library pool (kept cached between calls)
+// ---------------------------------------------------------------------------------------
+static cudaMemPool_t device_pool(int dev) {
+  static std::mutex mu;
+  static std::vector<cudaMemPool_t> pools;
+  std::lock_guard<std::mutex> lk(mu);
+  if ((int)pools.size() <= dev) pools.resize(dev + 1, nullptr);
+  if (pools[dev] == nullptr) {
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) return nullptr;
+    uint64_t thr = std::numeric_limits<uint64_t>::max();
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &thr);
+    pools[dev] = p;
+  }
+  return pools[dev];
+}
+
+static int pool_alloc(void** ptr, size_t bytes, int dev, cudaStream_t s) {
+  *ptr = nullptr;
+  if (bytes == 0) return WG_OK;
+  cudaMemPool_t pool = device_pool(dev);
+  if (pool == nullptr) return set_error(WG_ERR_CUDA, "cudaMemPoolCreate failed");
+  cudaError_t e = cudaMallocFromPoolAsync(ptr, bytes, pool, s);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return set_error(WG_ERR_OOM, "device allocation of %zu bytes failed", bytes);
+  }
+  if (e != cudaSuccess)
+    return set_error(WG_ERR_CUDA, "cudaMallocFromPoolAsync: %s", cudaGetErrorString(e));
+  return WG_OK;
+}
+
+static void pool_free(void* ptr, cudaStream_t s) {
+  if (ptr != nullptr) cudaFreeAsync(ptr, s);
+}
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// ---------------------------------------------------------------------------------------
+// plan
+// ---------------------------------------------------------------------------------------
+struct wg_plan {
+  PlanParams pp;
+  Geom g;
+  int prec = 0;
+  wg_options opt;
+  int device = 0;
+  int64_t nrows = 0, nchan = 0, nvis_total = 0, nvis = 0;
+  double umax = 0, vmax = 0, wmin = 0, wmax = 0;
+  // device data owned by the plan
+  double* chan4 = nullptr;
+  double* cinv_u = nullptr;
+  double* cinv_v = nullptr;
+  uint32_t* off = nullptr;
+  uint32_t* idx = nullptr;
+  uint32_t* meta = nullptr;
+  void* z = nullptr;
+  void* ph = nullptr;
+  size_t index_bytes = 0;
+  Coef<float> coef_f;
+  Coef<double> coef_d;
+  double psi_c[kPsiChebTerms];
+  // batching and FFT
+  int64_t batch = 1;
+  cufftHandle fft_full = 0, fft_rem = 0;
+  bool has_full = false, has_rem = false;
+  size_t fft_ws = 0;
+  size_t ws_bytes = 0;
+  std::mutex fft_mu;
+  cudaStream_t last_stream = nullptr;
+};
+
+static size_t cplx_bytes(int prec) { return prec ? 16 : 8; }
+
+void wg_default_options(wg_options* opt) {
+  if (opt == nullptr) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->do_wstacking = 1;
+  opt->w_shift = 1;
+  opt->eps_safety = 1.0;
+}
+
+static int free_plan_device(wg_plan* p) {
+  void* ptrs[] = {p->chan4, p->cinv_u, p->cinv_v, p->off, p->idx, p->meta, p->z, p->ph};
+  for (void* q : ptrs)
+    if (q != nullptr) cudaFree(q);
+  if (p->has_full) cufftDestroy(p->fft_full);
+  if (p->has_rem) cufftDestroy(p->fft_rem);
+  p->has_full = p->has_rem = false;
+  return WG_OK;
+}
+
+template <typename T>
+static int dev_alloc(T** ptr, size_t count) {
+  *ptr = nullptr;
+  if (count == 0) return WG_OK;
+  cudaError_t e = cudaMalloc((void**)ptr, count * sizeof(T));
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return set_error(WG_ERR_OOM, "cudaMalloc of %zu bytes failed", count * sizeof(T));
+  }
+  if (e != cudaSuccess) return set_error(WG_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(e));
+  return WG_OK;
+}
+
+static int make_fft(cufftHandle* h, int prec, int64_t nu, int64_t nv, int64_t batch,
+                    size_t* ws) {
+  WG_CUFFT(cufftCreate(h));
+  cufftResult r = cufftSetAutoAllocation(*h, 0);
+  if (r != CUFFT_SUCCESS) {
+    cufftDestroy(*h);
+    return set_error(WG_ERR_CUFFT, "cufftSetAutoAllocation: %d", (int)r);
+  }
+  long long n[2] = {(long long)nu, (long long)nv};
+  r = cufftMakePlanMany64(*h, 2, n, nullptr, 1, 0, nullptr, 1, 0, prec ? CUFFT_Z2Z : CUFFT_C2C,
+                          (long long)batch, ws);
+  if (r != CUFFT_SUCCESS) {
+    cufftDestroy(*h);
+    if (r == CUFFT_ALLOC_FAILED) return set_error(WG_ERR_OOM, "cuFFT plan allocation failed");
+    return set_error(WG_ERR_CUFFT, "cufftMakePlanMany64 (%lld x %lld x %lld): %d", n[0], n[1],
+                     (long long)batch, (int)r);
+  }
+  return WG_OK;
+}
+
+// per-call workspace layout
+struct Workspace {
+  size_t planes = 0, fft = 0, table = 0, acc = 0, total = 0;
+};
+
+static Workspace workspace_layout(const wg_plan* p, int64_t batch, size_t fft_ws) {
+  Workspace w;
+  w.planes = align_up((size_t)batch * p->pp.nu * p->pp.nv * cplx_bytes(p->prec), 256);
+  w.fft = align_up(fft_ws, 256);
+  w.table = align_up((size_t)p->g.nx * p->g.ny * 4 * (p->prec ? 8 : 4), 256);
+  w.acc = align_up((size_t)p->g.nx * p->g.ny * 8, 256);
+  w.total = w.planes + w.fft + w.table + w.acc;
+  return w;
+}
+
+static int build_index(wg_plan* p, const double* uvw, const uint8_t* mask, cudaStream_t s) {
+  const Geom& g = p->g;
+  const int64_t nkeys = (int64_t)g.ntu * g.ntv * g.nw;
+  if (nkeys + 1 > (int64_t)std::numeric_limits<uint32_t>::max())
+    return set_error(WG_ERR_ARG, "too many (tile, plane) buckets: %lld", (long long)nkeys);
+  if (p->nvis_total >= (int64_t)kFoldBit)
+    return set_error(WG_ERR_ARG, "at most 2^31 - 1 visibilities per plan");
+  WG_TRY(dev_alloc(&p->off, (size_t)nkeys + 1));
+  uint32_t *key = nullptr, *rank = nullptr, *scratch = nullptr;
+  int* err = nullptr;
+  int rc = WG_OK;
+  size_t nscr = scan_scratch_elems(nkeys + 1);
+  do {
+    if ((rc = pool_alloc((void**)&key, sizeof(uint32_t) * std::max<int64_t>(1, p->nvis_total),
+                         p->device, s)) != WG_OK) break;
+    if ((rc = pool_alloc((void**)&rank, sizeof(uint32_t) * std::max<int64_t>(1, p->nvis_total),
+                         p->device, s)) != WG_OK) break;
+    if ((rc = pool_alloc((void**)&scratch, sizeof(uint32_t) * nscr, p->device, s)) != WG_OK) break;
+    if ((rc = pool_alloc((void**)&err, sizeof(int), p->device, s)) != WG_OK) break;
+    cudaError_t e = cudaMemsetAsync(p->off, 0, sizeof(uint32_t) * (nkeys + 1), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = launch_bin_count(g, uvw, p->chan4, mask, p->off, key, rank, err, s);
+    if (e == cudaSuccess) e = launch_scan(p->off, nkeys + 1, scratch, s);
+    uint32_t nvalid = 0;
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nvalid, p->off + nkeys, sizeof(uint32_t),
+                                              cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { rc = set_error(WG_ERR_CUDA, "index build: %s", cudaGetErrorString(e)); break; }
+    if (herr != 0) { rc = set_error(WG_ERR_INTERNAL, "w-plane index out of range in index build"); break; }
+    p->nvis = nvalid;
+    size_t zsz = p->prec ? sizeof(Z4<double>) : sizeof(Z4<float>);
+    size_t phsz = cplx_bytes(p->prec);
+    size_t n = std::max<int64_t>(1, p->nvis);
+    if ((rc = dev_alloc(&p->idx, n)) != WG_OK) break;
+    if ((rc = dev_alloc(&p->meta, n)) != WG_OK) break;
+    if ((rc = dev_alloc((unsigned char**)&p->z, n * zsz)) != WG_OK) break;
+    bool use_ph = g.do_w && g.nshift != 0.0;
+    if (use_ph && (rc = dev_alloc((unsigned char**)&p->ph, n * phsz)) != WG_OK) break;
+    if (p->prec)
+      e = launch_bin_scatter<double>(g, uvw, p->chan4, key, rank, p->off, p->idx, p->meta,
+                                     (Z4<double>*)p->z, (double2*)p->ph, s);
+    else
+      e = launch_bin_scatter<float>(g, uvw, p->chan4, key, rank, p->off, p->idx, p->meta,
+                                    (Z4<float>*)p->z, (float2*)p->ph, s);
+    if (e != cudaSuccess) { rc = set_error(WG_ERR_CUDA, "index scatter: %s", cudaGetErrorString(e)); break; }
+    p->index_bytes = sizeof(uint32_t) * (nkeys + 1) + n * (8 + zsz + (use_ph ? phsz : 0));
+  } while (0);
+  pool_free(key, s); pool_free(rank, s); pool_free(scratch, s); pool_free(err, s);
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  if (rc == WG_OK && e2 != cudaSuccess)
+    rc = set_error(WG_ERR_CUDA, "index build: %s", cudaGetErrorString(e2));
+  return rc;
+}
+
+static PlanInput plan_input(int64_t npix_x, int64_t npix_y, double psx, double psy, double eps,
+                            int prec, const wg_options& o, double umax, double vmax,
+                            double wmin, double wmax, int64_t nvis) {
+  PlanInput in;
+  in.nx = npix_x; in.ny = npix_y; in.psx = psx; in.psy = psy; in.eps = eps; in.prec = prec;
+  in.do_w = o.do_wstacking; in.w_shift = o.w_shift; in.eps_safety = o.eps_safety;
+  in.force_alpha = o.force_alpha; in.force_sigma = o.force_sigma; in.tile = o.tile;
+  in.umax = umax; in.vmax = vmax; in.wmin = wmin; in.wmax = wmax; in.nvis = nvis;
+  return in;
+}
+
+static void fill_coefs(wg_plan* p) {
+  PolyKernel K = make_poly_kernel(p->pp.alpha, p->pp.beta, p->pp.mu, p->pp.alpha + 3);
+  std::memset(&p->coef_f, 0, sizeof(p->coef_f));
+  std::memset(&p->coef_d, 0, sizeof(p->coef_d));
+  for (int i = 0; i < K.alpha; ++i)
+    for (int d = 0; d <= K.deg; ++d) {
+      double c = K.c[(size_t)i * (K.deg + 1) + d];
+      p->coef_d.c[d * kMaxG + i] = c;
+      p->coef_f.c[d * kMaxG + i] = (float)c;
+    }
+  std::vector<double> pc = psi_cheb_coeffs(K, kPsiChebTerms);
+  for (int i = 0; i < kPsiChebTerms; ++i) p->psi_c[i] = pc[i];
+}
+
+int wg_plan_create(const double* uvw, const double* freq, int64_t nrows, int64_t nchan,
+                   int64_t npix_x, int64_t npix_y, double pixsize_x, double pixsize_y,
+                   double epsilon, int precision, const uint8_t* mask, const wg_options* opt,
+                   void* stream, wg_plan** out) {
+  if (out == nullptr) return set_error(WG_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (precision != WG_F32 && precision != WG_F64) return set_error(WG_ERR_ARG, "bad precision");
+  if (nrows < 0 || nchan < 1) return set_error(WG_ERR_ARG, "nrows must be >= 0 and nchan >= 1");
+  if ((nrows > 0 && uvw == nullptr) || freq == nullptr) return set_error(WG_ERR_ARG, "uvw / freq is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  std::unique_ptr<wg_plan> p(new wg_plan());
+  if (opt) p->opt = *opt; else wg_default_options(&p->opt);
+  if (p->opt.eps_safety <= 0) p->opt.eps_safety = 1.0;
+  p->prec = precision;
+  p->nrows = nrows; p->nchan = nchan; p->nvis_total = nrows * nchan;
+  WG_CUDA(cudaGetDevice(&p->device));
+
+  // channel frequencies and the uvw extent (device reduction)
+  std::vector<double> f(nchan);
+  WG_CUDA(cudaMemcpyAsync(f.data(), freq, sizeof(double) * nchan, cudaMemcpyDeviceToHost, s));
+  unsigned long long* ext = nullptr;
+  unsigned long long hext[4] = {0ull, 0ull, (unsigned long long)0x7fefffffffffffffull, 0ull};
+  WG_TRY(pool_alloc((void**)&ext, sizeof(hext), p->device, s));
+  WG_CUDA(cudaMemcpyAsync(ext, hext, sizeof(hext), cudaMemcpyHostToDevice, s));
+  if (nrows > 0) WG_CUDA(launch_extent(uvw, nrows, ext, s));
+  WG_CUDA(cudaMemcpyAsync(hext, ext, sizeof(hext), cudaMemcpyDeviceToHost, s));
+  pool_free(ext, s);
+  WG_CUDA(cudaStreamSynchronize(s));
+  double fmin = std::numeric_limits<double>::max(), fmax = 0.0;
+  for (double v : f) {
+    if (!(v > 0.0) || !std::isfinite(v)) return set_error(WG_ERR_ARG, "frequencies must be positive");
+    fmin = std::min(fmin, v); fmax = std::max(fmax, v);
+  }
+  double ext_d[4];
+  for (int i = 0; i < 4; ++i) std::memcpy(&ext_d[i], &hext[i], sizeof(double));
+  if (nrows == 0) ext_d[2] = 0.0;
+  if (!std::isfinite(ext_d[0]) || !std::isfinite(ext_d[1]) || !std::isfinite(ext_d[3]))
+    return set_error(WG_ERR_ARG, "uvw contains non-finite values");
+  p->umax = ext_d[0] * fmax / kSpeedOfLight;
+  p->vmax = ext_d[1] * fmax / kSpeedOfLight;
+  p->wmin = p->opt.do_wstacking ? ext_d[2] * fmin / kSpeedOfLight : 0.0;
+  p->wmax = p->opt.do_wstacking ? ext_d[3] * fmax / kSpeedOfLight : 0.0;
+  if (p->umax * pixsize_x > 1e6 || p->vmax * pixsize_y > 1e6)
+    return set_error(WG_ERR_ARG, "uv coordinates too large for the pixel size (|u| dl > 1e6)");
+
+  char err[256];
+  PlanInput in = plan_input(npix_x, npix_y, pixsize_x, pixsize_y, epsilon, precision, p->opt,
+                            p->umax, p->vmax, p->wmin, p->wmax, p->nvis_total);
+  if (choose_plan(in, p->pp, err, sizeof(err)) != 0) return set_error(WG_ERR_ARG, "%s", err);
+  const PlanParams& pp = p->pp;
+  Geom& g = p->g;
+  g.nrows = nrows; g.nchan = nchan; g.nvis = p->nvis_total;
+  g.nx = (int)npix_x; g.ny = (int)npix_y;
+  g.nu = (int)pp.nu; g.nv = (int)pp.nv; g.nw = (int)pp.nw;
+  g.tile = pp.tile; g.ntu = (int)pp.ntu; g.ntv = (int)pp.ntv;
+  g.alpha = pp.alpha; g.deg = pp.alpha + 3;
+  g.do_w = p->opt.do_wstacking ? 1 : 0;
+  g.alpha_w = g.do_w ? pp.alpha : 1;
+  g.psx = pixsize_x; g.psy = pixsize_y;
+  g.w0 = pp.w0; g.dw = pp.dw; g.nshift = pp.nshift;
+  g.w0_dw = pp.w0 / pp.dw;
+  fill_coefs(p.get());
+
+  int rc = WG_OK;
+  auto fail = [&](int code) { free_plan_device(p.get()); return code; };
+  // per-channel scales and the per-axis correction 1 / psi
+  {
+    std::vector<double> c4(4 * nchan);
+    for (int64_t ch = 0; ch < nchan; ++ch) {
+      double s_ = f[ch] / kSpeedOfLight;
+      c4[4 * ch + 0] = s_ * pixsize_x * pp.nu;
+      c4[4 * ch + 1] = s_ * pixsize_y * pp.nv;
+      c4[4 * ch + 2] = s_ / pp.dw;
+      c4[4 * ch + 3] = s_;
+    }
+    std::vector<double> cu(npix_x), cv(npix_y);
+    std::vector<double> pc(p->psi_c, p->psi_c + kPsiChebTerms);
+    for (int64_t j = 0; j < npix_x; ++j)
+      cu[j] = 1.0 / psi_cheb_eval(pc, (double)(j - npix_x / 2) / pp.nu);
+    for (int64_t j = 0; j < npix_y; ++j)
+      cv[j] = 1.0 / psi_cheb_eval(pc, (double)(j - npix_y / 2) / pp.nv);
+    if ((rc = dev_alloc(&p->chan4, c4.size())) != WG_OK) return fail(rc);
+    if ((rc = dev_alloc(&p->cinv_u, cu.size())) != WG_OK) return fail(rc);
+    if ((rc = dev_alloc(&p->cinv_v, cv.size())) != WG_OK) return fail(rc);
+    cudaError_t e = cudaMemcpy(p->chan4, c4.data(), sizeof(double) * c4.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->cinv_u, cu.data(), sizeof(double) * cu.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->cinv_v, cv.data(), sizeof(double) * cv.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(set_error(WG_ERR_CUDA, "upload: %s", cudaGetErrorString(e)));
+  }
+  if ((rc = build_index(p.get(), uvw, mask, s)) != WG_OK) return fail(rc);
+
+  // batch of planes: as many as the workspace budget allows
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return fail(set_error(WG_ERR_CUDA, "cudaMemGetInfo"));
+  size_t budget = p->opt.max_workspace;
+  if (budget == 0) budget = std::min<size_t>(free_b / 2, (size_t)48 << 30);
+  const size_t plane_b = (size_t)pp.nu * pp.nv * cplx_bytes(precision);
+  int64_t B = std::max<int64_t>(1, std::min<int64_t>(pp.nw, (int64_t)(budget / (2 * plane_b))));
+  for (;;) {
+    size_t ws = 0;
+    if ((rc = make_fft(&p->fft_full, precision, pp.nu, pp.nv, B, &ws)) != WG_OK) {
+      if (rc == WG_ERR_OOM && B > 1) { B = std::max<int64_t>(1, B / 2); continue; }
+      return fail(rc);
+    }
+    p->has_full = true;
+    Workspace w = workspace_layout(p.get(), B, ws);
+    if (w.total <= budget || B == 1) { p->fft_ws = ws; break; }
+    cufftDestroy(p->fft_full); p->has_full = false;
+    B = std::max<int64_t>(1, B * 3 / 4);
+  }
+  p->batch = B;
+  int64_t rem = pp.nw % B;
+  if (rem != 0) {
+    size_t ws = 0;
+    if ((rc = make_fft(&p->fft_rem, precision, pp.nu, pp.nv, rem, &ws)) != WG_OK) return fail(rc);
+    p->has_rem = true;
+    p->fft_ws = std::max(p->fft_ws, ws);
+  }
+  p->ws_bytes = workspace_layout(p.get(), B, p->fft_ws).total;
+  if (p->opt.max_workspace != 0 && p->ws_bytes > p->opt.max_workspace)
+    return fail(set_error(WG_ERR_OOM, "one w-plane needs %zu bytes of workspace, above the cap %zu",
+                          p->ws_bytes, (size_t)p->opt.max_workspace));
+  p->last_stream = s;
+  *out = p.release();
+  return WG_OK;
+}
+
+int wg_plan_destroy(wg_plan* plan) {
+  if (plan == nullptr) return WG_OK;
+  cudaStreamSynchronize(plan->last_stream);
+  free_plan_device(plan);
+  delete plan;
+  return WG_OK;
+}
+
+int wg_plan_get_info(const wg_plan* p, wg_plan_info* info) {
+  if (p == nullptr || info == nullptr) return set_error(WG_ERR_ARG, "NULL argument");
+  std::memset(info, 0, sizeof(*info));
+  info->alpha = p->pp.alpha; info->sigma = p->pp.sigma; info->beta = p->pp.beta;
+  info->mu = p->pp.mu; info->eps_kernel = p->pp.eps_kernel;
+  info->nu = p->pp.nu; info->nv = p->pp.nv; info->nw = p->pp.nw;
+  info->dw = p->pp.dw; info->w0 = p->pp.w0; info->nshift = p->pp.nshift;
+  info->tile = p->pp.tile; info->ntiles = p->pp.ntu * p->pp.ntv;
+  info->nvis = p->nvis; info->batch = p->batch;
+  info->index_bytes = p->index_bytes; info->workspace_bytes = p->ws_bytes;
+  info->umax = p->umax; info->vmax = p->vmax; info->wmin = p->wmin; info->wmax = p->wmax;
+  return WG_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// per-stage timing
+// ---------------------------------------------------------------------------------------
+struct StageTimer {
+  bool on = false;
+  cudaStream_t s = nullptr;
+  std::vector<std::pair<int, cudaEvent_t>> marks;  // (stage entered, event)
+  cudaEvent_t t0 = nullptr;
+  void start(bool enable, cudaStream_t st) {
+    on = enable; s = st;
+    if (!on) return;
+    cudaEventCreate(&t0);
+    cudaEventRecord(t0, s);
+  }
+  // record the end of a stage
+  void mark(int stage) {
+    if (!on) return;
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, s);
+    marks.emplace_back(stage, e);
+  }
+  void finish(wg_stats* st) {
+    if (!on) return;
+    cudaEventSynchronize(marks.empty() ? t0 : marks.back().second);
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    cudaEvent_t prev = t0;
+    for (auto& m : marks) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, prev, m.second);
+      acc[m.first] += ms;
+      prev = m.second;
+    }
+    float tot = 0.f;
+    if (!marks.empty()) cudaEventElapsedTime(&tot, t0, marks.back().second);
+    st->ms_total = tot;
+    st->ms_prep = acc[0]; st->ms_screen = acc[1]; st->ms_fft = acc[2];
+    st->ms_grid = acc[3]; st->ms_accum = acc[4];
+    for (auto& m : marks) cudaEventDestroy(m.second);
+    cudaEventDestroy(t0);
+  }
+};
+enum { ST_PREP = 0, ST_SCREEN = 1, ST_FFT = 2, ST_GRID = 3, ST_ACCUM = 4, ST_OTHER = 5 };
+
+static int run_fft(wg_plan* p, int64_t nb, void* data, void* work, int dir, cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(p->fft_mu);
+  cufftHandle h = (nb == p->batch) ? p->fft_full : p->fft_rem;
+  if (nb != p->batch && !p->has_rem) return set_error(WG_ERR_INTERNAL, "no FFT plan for %lld planes", (long long)nb);
+  WG_CUFFT(cufftSetStream(h, s));
+  WG_CUFFT(cufftSetWorkArea(h, work));
+  if (p->prec)
+    WG_CUFFT(cufftExecZ2Z(h, (cufftDoubleComplex*)data, (cufftDoubleComplex*)data, dir));
+  else
+    WG_CUFFT(cufftExecC2C(h, (cufftComplex*)data, (cufftComplex*)data, dir));
+  return WG_OK;
+}
+
+template <typename R>
+static int degrid_impl(wg_plan* p, const R* dirty, const R* wgt, typename C2<R>::T* vis,
+                       cudaStream_t s, wg_stats* stats) {
+  StageTimer tm;
+  tm.start(stats != nullptr, s);
+  const Geom& g = p->g;
+  if (p->nvis_total > 0)
+    WG_CUDA(cudaMemsetAsync(vis, 0, sizeof(typename C2<R>::T) * p->nvis_total, s));
+  if (p->nvis == 0) {
+    tm.mark(ST_OTHER);
+    if (stats) { std::memset(stats, 0, sizeof(*stats)); tm.finish(stats); }
+    return WG_OK;
+  }
+  Workspace w = workspace_layout(p, p->batch, p->fft_ws);
+  unsigned char* ws = nullptr;
+  WG_TRY(pool_alloc((void**)&ws, w.total, p->device, s));
+  auto* planes = (typename C2<R>::T*)ws;
+  void* fftw = ws + w.planes;
+  auto* table = (Z4<R>*)(ws + w.planes + w.fft);
+  int rc = WG_OK;
+  ImgParams ip;
+  ip.g = g;
+  std::memcpy(ip.psi_c, p->psi_c, sizeof(ip.psi_c));
+  ip.cinv_u = p->cinv_u; ip.cinv_v = p->cinv_v;
+  IndexView<R> ix{p->off, p->idx, p->meta, (const Z4<R>*)p->z, (const typename C2<R>::T*)p->ph};
+  const Coef<R>& coef = *reinterpret_cast<const Coef<R>*>(sizeof(R) == 4 ? (const void*)&p->coef_f
+                                                                         : (const void*)&p->coef_d);
+  int64_t nbatches = 0;
+  do {
+    cudaError_t e = launch_prep<R>(ip, dirty, table, s);
+    if (e != cudaSuccess) { rc = set_error(WG_ERR_CUDA, "prep: %s", cudaGetErrorString(e)); break; }
+    tm.mark(ST_PREP);
+    for (int64_t b0 = 0; b0 < g.nw; b0 += p->batch) {
+      int nb = (int)std::min<int64_t>(p->batch, g.nw - b0);
+      e = launch_screen<R>(g, table, planes, (int)b0, nb, s);
+      if (e != cudaSuccess) { rc = set_error(WG_ERR_CUDA, "screen: %s", cudaGetErrorString(e)); break; }
+      tm.mark(ST_SCREEN);
+      if ((rc = run_fft(p, nb, planes, fftw, CUFFT_FORWARD, s)) != WG_OK) break;
+      tm.mark(ST_FFT);
+      e = launch_degrid<R>(g, coef, ix, planes, (int)b0, nb, wgt, vis, s);
+      if (e != cudaSuccess) { rc = set_error(WG_ERR_CUDA, "degrid: %s", cudaGetErrorString(e)); break; }
+      tm.mark(ST_GRID);
+      ++nbatches;
+    }
+  } while (0);
+  pool_free(ws, s);
+  p->last_stream = s;
+  if (rc != WG_OK) return rc;
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    tm.finish(stats);
+    stats->n_batches = nbatches; stats->n_planes = g.nw; stats->workspace_bytes = w.total;
+  }
+  return WG_OK;
+}
+
+template <typename R>
+static int grid_impl(wg_plan* p, const typename C2<R>::T* vis, const R* wgt, R* dirty,
+                     cudaStream_t s, wg_stats* stats) {
+  StageTimer tm;
+  tm.start(stats != nullptr, s);
+  const Geom& g = p->g;
+  if (p->nvis == 0) {
+    WG_CUDA(cudaMemsetAsync(dirty, 0, sizeof(R) * g.nx * g.ny, s));
+    tm.mark(ST_OTHER);
+    if (stats) { std::memset(stats, 0, sizeof(*stats)); tm.finish(stats); }
+    return WG_OK;
+  }
+  Workspace w = workspace_layout(p, p->batch, p->fft_ws);
+  unsigned char* ws = nullptr;
+  WG_TRY(pool_alloc((void**)&ws, w.total, p->device, s));
+  auto* planes = (typename C2<R>::T*)ws;
+  void* fftw = ws + w.planes;
+  auto* table = (Z4<R>*)(ws + w.planes + w.fft);
+  auto* acc = (double*)(ws + w.planes + w.fft + w.table);
+  int rc = WG_OK;
+  ImgParams ip;
+  ip.g = g;
+  std::memcpy(ip.psi_c, p->psi_c, sizeof(ip.psi_c));
+  ip.cinv_u = p->cinv_u; ip.cinv_v = p->cinv_v;
+  IndexView<R> ix{p->off, p->idx, p->meta, (const Z4<R>*)p->z, (const typename C2<R>::T*)p->ph};
+  const Coef<R>& coef = *reinterpret_cast<const Coef<R>*>(sizeof(R) == 4 ? (const void*)&p->coef_f
+                                                                         : (const void*)&p->coef_d);
+  int64_t nbatches = 0;
+  do {
+    cudaError_t e = launch_prep<R>(ip, nullptr, table, s);
+    if (e != cudaSuccess) { rc = set_error(WG_ERR_CUDA, "prep: %s", cudaGetErrorString(e)); break; }
+    tm.mark(ST_PREP);
+    for (int64_t b0 = 0; b0 < g.nw; b0 += p->batch) {
+      int nb = (int)std::min<int64_t>(p->batch, g.nw - b0);
+      e = launch_grid<R>(g, coef, ix, vis, wgt, planes, (int)b0, nb, s);
+      if (e != cudaSuccess) { rc = set_error(WG_ERR_CUDA, "grid: %s", cudaGetErrorString(e)); break; }
+      tm.mark(ST_GRID);
+      if ((rc = run_fft(p, nb, planes, fftw, CUFFT_INVERSE, s)) != WG_OK) break;
+      tm.mark(ST_FFT);
+      e = launch_accumulate<R>(g, table, planes, (int)b0, nb, acc, b0 == 0,
+                               b0 + nb >= g.nw, dirty, s);
+      if (e != cudaSuccess) { rc = set_error(WG_ERR_CUDA, "accumulate: %s", cudaGetErrorString(e)); break; }
+      tm.mark(ST_ACCUM);
+      ++nbatches;
+    }
+  } while (0);
+  pool_free(ws, s);
+  p->last_stream = s;
+  if (rc != WG_OK) return rc;
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    tm.finish(stats);
+    stats->n_batches = nbatches; stats->n_planes = g.nw; stats->workspace_bytes = w.total;
+  }
+  return WG_OK;
+}
+
+int wg_degrid(wg_plan* plan, const void* dirty, const void* wgt, void* vis, void* stream,
+              wg_stats* stats) {
+  if (plan == nullptr || dirty == nullptr || (vis == nullptr && plan->nvis_total > 0))
+    return set_error(WG_ERR_ARG, "NULL plan / dirty / vis");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (plan->prec)
+    return degrid_impl<double>(plan, (const double*)dirty, (const double*)wgt, (double2*)vis, s, stats);
+  return degrid_impl<float>(plan, (const float*)dirty, (const float*)wgt, (float2*)vis, s, stats);
+}
+
+int wg_grid(wg_plan* plan, const void* vis, const void* wgt, void* dirty, void* stream,
+            wg_stats* stats) {
+  if (plan == nullptr || dirty == nullptr || (vis == nullptr && plan->nvis_total > 0))
+    return set_error(WG_ERR_ARG, "NULL plan / vis / dirty");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (plan->prec)
+    return grid_impl<double>(plan, (const double2*)vis, (const double*)wgt, (double*)dirty, s, stats);
+  return grid_impl<float>(plan, (const float2*)vis, (const float*)wgt, (float*)dirty, s, stats);
+}
+
+int wg_dirty2ms(const double* uvw, const double* freq, int64_t nrows, int64_t nchan,
+                const void* dirty, const void* wgt, int64_t npix_x, int64_t npix_y,
+                double pixsize_x, double pixsize_y, double epsilon, int precision,
+                int do_wstacking, const uint8_t* mask, void* vis, void* stream) {
+  wg_options o;
+  wg_default_options(&o);
+  o.do_wstacking = do_wstacking;
+  wg_plan* p = nullptr;
+  WG_TRY(wg_plan_create(uvw, freq, nrows, nchan, npix_x, npix_y, pixsize_x, pixsize_y, epsilon,
+                        precision, mask, &o, stream, &p));
+  int rc = wg_degrid(p, dirty, wgt, vis, stream, nullptr);
+  std::string keep = g_last_error;
+  wg_plan_destroy(p);
+  g_last_error = keep;
+  return rc;
+}
+
+int wg_ms2dirty(const double* uvw, const double* freq, int64_t nrows, int64_t nchan,
+                const void* vis, const void* wgt, int64_t npix_x, int64_t npix_y,
+                double pixsize_x, double pixsize_y, double epsilon, int precision,
+                int do_wstacking, const uint8_t* mask, void* dirty, void* stream) {
+  wg_options o;
+  wg_default_options(&o);
+  o.do_wstacking = do_wstacking;
+  wg_plan* p = nullptr;
+  WG_TRY(wg_plan_create(uvw, freq, nrows, nchan, npix_x, npix_y, pixsize_x, pixsize_y, epsilon,
+                        precision, mask, &o, stream, &p));
+  int rc = wg_grid(p, vis, wgt, dirty, stream, nullptr);
+  std::string keep = g_last_error;
+  wg_plan_destroy(p);
+  g_last_error = keep;
+  return rc;
+}
+
+const char* wg_last_error(void) { return g_last_error.c_str(); }
+
+// ---------------------------------------------------------------------------------------
+// host-only helpers
+// ---------------------------------------------------------------------------------------
+int wg_kernel_table_size(void) { return (int)kernel_table().size(); }
+
+int wg_kernel_table_row(int i, int* alpha, double* sigma, double* eps, double* beta, double* mu) {
+  const auto& T = kernel_table();
+  if (i < 0 || i >= (int)T.size()) return set_error(WG_ERR_ARG, "row %d out of range", i);
+  if (alpha) *alpha = T[i].alpha;
+  if (sigma) *sigma = T[i].sigma;
+  if (eps) *eps = T[i].eps;
+  if (beta) *beta = T[i].beta;
+  if (mu) *mu = T[i].mu;
+  return WG_OK;
+}
+
+int wg_kernel_phi(int alpha, double beta, double mu, const double* x, double* out, int64_t n) {
+  if (alpha < 1 || alpha > kMaxAlpha || !x || !out) return set_error(WG_ERR_ARG, "bad arguments");
+  for (int64_t i = 0; i < n; ++i) out[i] = es_phi(alpha, beta, mu, x[i]);
+  return WG_OK;
+}
+
+int wg_kernel_poly(int alpha, double beta, double mu, const double* x, double* out, int64_t n) {
+  if (alpha < 1 || alpha > kMaxAlpha || !x || !out) return set_error(WG_ERR_ARG, "bad arguments");
+  PolyKernel K = make_poly_kernel(alpha, beta, mu, alpha + 3);
+  for (int64_t i = 0; i < n; ++i) out[i] = K.eval(x[i]);
+  return WG_OK;
+}
+
+int wg_kernel_psi(int alpha, double beta, double mu, const double* k, double* out, int64_t n) {
+  if (alpha < 1 || alpha > kMaxAlpha || !k || !out) return set_error(WG_ERR_ARG, "bad arguments");
+  PolyKernel K = make_poly_kernel(alpha, beta, mu, alpha + 3);
+  for (int64_t i = 0; i < n; ++i) out[i] = psi_poly(K, k[i]);
+  return WG_OK;
+}
+
+int wg_plan_params(int64_t npix_x, int64_t npix_y, double pixsize_x, double pixsize_y,
+                   double epsilon, int precision, const wg_options* opt, double umax,
+                   double vmax, double wmin, double wmax, int64_t nvis, wg_plan_info* info) {
+  if (info == nullptr) return set_error(WG_ERR_ARG, "info is NULL");
+  wg_options o;
+  if (opt) o = *opt; else wg_default_options(&o);
+  if (o.eps_safety <= 0) o.eps_safety = 1.0;
+  PlanInput in = plan_input(npix_x, npix_y, pixsize_x, pixsize_y, epsilon, precision, o, umax,
+                            vmax, wmin, wmax, nvis);
+  PlanParams pp;
+  char err[256];
+  if (choose_plan(in, pp, err, sizeof(err)) != 0) return set_error(WG_ERR_ARG, "%s", err);
+  std::memset(info, 0, sizeof(*info));
+  info->alpha = pp.alpha; info->sigma = pp.sigma; info->beta = pp.beta; info->mu = pp.mu;
+  info->eps_kernel = pp.eps_kernel; info->nu = pp.nu; info->nv = pp.nv; info->nw = pp.nw;
+  info->dw = pp.dw; info->w0 = pp.w0; info->nshift = pp.nshift; info->tile = pp.tile;
+  info->ntiles = pp.ntu * pp.ntv; info->nvis = nvis;
+  info->umax = umax; info->vmax = vmax; info->wmin = wmin; info->wmax = wmax;
+  return WG_OK;
+}
+
+const char* wg_version(void) { return "wgrid-gb300 0.1 (sm_103a)"; }

@@ -1,0 +1,102 @@
+// Internal declarations of the GB300 w-gridder: plan layout, kernel parameter blocks and
+// kernel launchers.  Not part of the public ABI (see include/wgrid.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <cstdint>
+#include <mutex>
+#include <vector>
+
+#include "host_math.h"
+#include "wgrid.h"
+
+namespace wg {
+
+template <typename R> struct C2;
+template <> struct C2<float> { using T = float2; };
+template <> struct C2<double> { using T = double2; };
+
+// Per-visibility record of the on-device index, in tile-sorted order (structure of arrays).
+//   idx:  k | (folded << 31)           (k = row * nchan + chan)
+//   meta: du | dv << 8 | c0 << 16      (first cell inside the source tile, first w-plane)
+//   z:    Horner coordinates zu, zv, zw in [-1, 1) of the first kernel piece (Sec. 4.2)
+//   ph:   exp(2 pi i w_k nshift) (only when the w reference is shifted)
+template <typename R> struct alignas(4 * sizeof(R)) Z4 { R u, v, w, pad; };
+
+constexpr uint32_t kFoldBit = 0x80000000u;
+
+// Geometry shared by all device kernels of a plan (passed by value).
+struct Geom {
+  int64_t nrows, nchan, nvis;
+  int nx, ny;
+  int nu, nv, nw;
+  int tile, ntu, ntv;
+  int alpha, deg;
+  int do_w;
+  int alpha_w;          // alpha when w-gridding, 1 otherwise (a single plane, weight 1)
+  double psx, psy;
+  double w0, dw, nshift;
+  double w0_dw;         // w0 / dw
+};
+
+// Kernel polynomial coefficients, layout [d][G] so lane j reads c[d * kMaxG + j].
+constexpr int kMaxG = 16;
+template <typename R> struct Coef { R c[(kMaxDeg + 1) * kMaxG]; };
+
+// psi_w Chebyshev coefficients (in y = 8 k^2 - 1) and per-axis correction tables.
+struct ImgParams {
+  Geom g;
+  double psi_c[kPsiChebTerms];
+  const double* cinv_u;  // (nx) 1 / psi_u((jx - nx/2) / nu)
+  const double* cinv_v;  // (ny)
+};
+
+template <typename R>
+struct IndexView {
+  const uint32_t* off;     // (ntiles * nw + 1) start of bucket (tile, c0)
+  const uint32_t* idx;
+  const uint32_t* meta;
+  const Z4<R>* z;
+  const typename C2<R>::T* ph;  // may be null
+};
+
+struct PlanImpl;
+
+// ---- index kernels (kernels_index.cu) ------------------------------------------------
+cudaError_t launch_extent(const double* uvw, int64_t nrows, unsigned long long* ext4,
+                          cudaStream_t s);
+cudaError_t launch_bin_count(const Geom& g, const double* uvw, const double* chan4,
+                             const uint8_t* mask, uint32_t* hist, uint32_t* key,
+                             uint32_t* rank, int* err, cudaStream_t s);
+cudaError_t launch_scan(uint32_t* data, int64_t n, uint32_t* scratch, cudaStream_t s);
+size_t scan_scratch_elems(int64_t n);
+template <typename R>
+cudaError_t launch_bin_scatter(const Geom& g, const double* uvw, const double* chan4,
+                               const uint32_t* key, const uint32_t* rank, const uint32_t* off,
+                               uint32_t* idx, uint32_t* meta, Z4<R>* z,
+                               typename C2<R>::T* ph, cudaStream_t s);
+
+// ---- image-side kernels (kernels_image.cu) -------------------------------------------
+// table: per pixel (value, A, Bhi, Blo) for f32, (value, A, B, 0) for f64.
+template <typename R>
+cudaError_t launch_prep(const ImgParams& P, const R* dirty, Z4<R>* table, cudaStream_t s);
+template <typename R>
+cudaError_t launch_screen(const Geom& g, const Z4<R>* table, typename C2<R>::T* planes,
+                          int b0, int nb, cudaStream_t s);
+template <typename R>
+cudaError_t launch_accumulate(const Geom& g, const Z4<R>* table,
+                              const typename C2<R>::T* planes, int b0, int nb, double* acc,
+                              bool first, bool last, R* dirty, cudaStream_t s);
+
+// ---- (de)gridding kernels (kernels_grid.cu) ------------------------------------------
+template <typename R>
+cudaError_t launch_degrid(const Geom& g, const Coef<R>& coef, const IndexView<R>& ix,
+                          const typename C2<R>::T* planes, int b0, int nb, const R* wgt,
+                          typename C2<R>::T* vis, cudaStream_t s);
+template <typename R>
+cudaError_t launch_grid(const Geom& g, const Coef<R>& coef, const IndexView<R>& ix,
+                        const typename C2<R>::T* vis, const R* wgt,
+                        typename C2<R>::T* planes, int b0, int nb, cudaStream_t s);
+
+}  // namespace wg

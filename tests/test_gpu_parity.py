@@ -1,0 +1,221 @@
+"""GPU parity: libwgrid.so (through its C ABI) against the FP64 direct-sum oracle.
+
+The method approximates R0 (Eq. rime) and R0^dagger to a requested epsilon; the bar is the
+paper's accuracy measure (Sec. 6.2, eps_rms = relative L2 error against the direct sum) at or
+below the requested epsilon, on the same seeded inputs, plus the adjointness criterion of
+Sec. 6.1 (eps_adj < 1e-7 single, < 1e-14 double; the paper reports < 1e-15 for double).
+Small cases span several uv tiles with ragged visibility counts; full-size workloads are
+checked on sampled outputs the oracle computes one by one.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2010_10122_gb300 import synthetic as S  # noqa: E402
+
+ADJ_TOL = {"f32": 1e-7, "f64": 1e-14}
+
+
+@pytest.fixture(scope="module")
+def wg():
+    from paper_2010_10122_gb300 import _build
+    _build.build()
+    import paper_2010_10122_gb300 as wg
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return wg
+
+
+def _dt(prec):
+    return (np.float32, np.complex64) if prec == "f32" else (np.float64, np.complex128)
+
+
+def _cu(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def run_pair(wg, obs, eps, prec, I, d, wgt=None, mask=None, **opts):
+    rdt, cdt = _dt(prec)
+    plan = wg.Plan(obs.uvw, obs.freq, obs.npix_x, obs.npix_y, obs.pixsize_x, obs.pixsize_y, eps,
+                   prec, mask=mask, **opts)
+    w = None if wgt is None else _cu(wgt.astype(rdt))
+    vis = plan.degrid(_cu(I.astype(rdt)), wgt=w).cpu().numpy()
+    img = plan.grid(_cu(d.astype(cdt)), wgt=w).cpu().numpy()
+    return plan, vis, img
+
+
+def oracle_pair(oracle_lib, obs, I, d, wgt=None, mask=None, do_wstacking=True):
+    rv = oracle_lib.degrid(obs.uvw, obs.freq, I, obs.pixsize_x, obs.pixsize_y, wgt=wgt,
+                           mask=mask, do_wstacking=do_wstacking)
+    ri = oracle_lib.grid(obs.uvw, obs.freq, d, obs.npix_x, obs.npix_y, obs.pixsize_x,
+                         obs.pixsize_y, wgt=wgt, mask=mask, do_wstacking=do_wstacking)
+    return rv, ri
+
+
+SMALL = S.random_uvw_observation(701, 3, 96, 128, 25.0, seed=3)  # 2103 vis, several tiles
+
+
+@pytest.fixture(scope="module")
+def small_ref(oracle_lib):
+    I = S.gaussian_image(SMALL.npix_x, SMALL.npix_y, seed=1)
+    d = S.complex_normal((SMALL.nrows, SMALL.nchan), seed=2)
+    rv, ri = oracle_pair(oracle_lib, SMALL, I, d)
+    return I, d, rv, ri
+
+
+@pytest.mark.parametrize("w_shift", [1, 0])
+@pytest.mark.parametrize("prec,eps", [("f64", 1e-12), ("f64", 1e-10), ("f64", 1e-7),
+                                      ("f64", 1e-3), ("f32", 1e-5), ("f32", 1e-4),
+                                      ("f32", 1e-3)])
+def test_small_matches_oracle(wg, oracle_lib, small_ref, prec, eps, w_shift):
+    I, d, rv, ri = small_ref
+    plan, vis, img = run_pair(wg, SMALL, eps, prec, I, d, w_shift=w_shift)
+    ev, ei = oracle_lib.rel_l2(vis, rv), oracle_lib.rel_l2(img, ri)
+    assert ev <= eps and ei <= eps, (ev, ei, plan.info)
+    adj = oracle_lib.adjointness_error(I, vis, d, img)
+    assert adj < ADJ_TOL[prec]
+
+
+@pytest.mark.parametrize("alpha", [4, 7, 8, 12, 16])
+def test_every_kernel_support(wg, oracle_lib, small_ref, alpha):
+    """Force each tabulated support (G = 4, 8, 16 lane groups, tiles 16 and 32)."""
+    I, d, rv, ri = small_ref
+    eps = {4: 3e-2, 7: 1e-3, 8: 1e-4, 12: 1e-6, 16: 1e-9}[alpha]
+    plan, vis, img = run_pair(wg, SMALL, eps, "f64", I, d, force_alpha=alpha)
+    assert plan.info["alpha"] == alpha
+    assert oracle_lib.rel_l2(vis, rv) <= eps and oracle_lib.rel_l2(img, ri) <= eps
+
+
+@pytest.mark.parametrize("tile", [16, 32])
+def test_tile_sizes_agree(wg, oracle_lib, small_ref, tile):
+    I, d, rv, ri = small_ref
+    plan, vis, img = run_pair(wg, SMALL, 1e-5, "f32", I, d, tile=tile)
+    assert plan.info["tile"] == tile
+    assert oracle_lib.rel_l2(vis, rv) <= 1e-5 and oracle_lib.rel_l2(img, ri) <= 1e-5
+
+
+def test_weights_and_mask(wg, oracle_lib):
+    obs = S.random_uvw_observation(333, 4, 64, 64, 30.0, seed=9)
+    I = S.gaussian_image(64, 64, seed=4)
+    d = S.complex_normal((333, 4), seed=5)
+    rng = np.random.default_rng(7)
+    wgt = rng.uniform(0.2, 2.0, (333, 4))
+    mask = (rng.uniform(size=(333, 4)) > 0.3).astype(np.uint8)
+    for prec, eps in (("f64", 1e-10), ("f32", 1e-5)):
+        _, vis, img = run_pair(wg, obs, eps, prec, I, d, wgt=wgt, mask=mask)
+        rv, ri = oracle_pair(oracle_lib, obs, I, d, wgt=wgt, mask=mask)
+        assert oracle_lib.rel_l2(vis, rv) <= eps and oracle_lib.rel_l2(img, ri) <= eps
+        assert np.all(vis[mask == 0] == 0)
+
+
+def test_no_wstacking(wg, oracle_lib):
+    obs = S.random_uvw_observation(400, 2, 64, 96, 20.0, seed=11)
+    I = S.gaussian_image(64, 96, seed=6)
+    d = S.complex_normal((400, 2), seed=7)
+    for prec, eps in (("f64", 1e-9), ("f32", 1e-5)):
+        plan, vis, img = run_pair(wg, obs, eps, prec, I, d, do_wstacking=False)
+        assert plan.info["nw"] == 1
+        rv, ri = oracle_pair(oracle_lib, obs, I, d, do_wstacking=False)
+        assert oracle_lib.rel_l2(vis, rv) <= eps and oracle_lib.rel_l2(img, ri) <= eps
+
+
+def test_tiny_workload_full(wg, oracle_lib):
+    """256^2 image, 1e4 visibilities, eps = 1e-10 FP64: every output against the oracle."""
+    obs = S.tiny()
+    I = S.gaussian_image(obs.npix_x, obs.npix_y, seed=1)
+    d = S.complex_normal((obs.nrows, obs.nchan), seed=2)
+    _, vis, img = run_pair(wg, obs, 1e-10, "f64", I, d)
+    rv, ri = oracle_pair(oracle_lib, obs, I, d)
+    assert oracle_lib.rel_l2(vis, rv) <= 1e-10
+    assert oracle_lib.rel_l2(img, ri) <= 1e-10
+    assert oracle_lib.adjointness_error(I, vis, d, img) < 1e-14
+
+
+@pytest.mark.parametrize("prec,eps", [("f32", 1e-5), ("f64", 1e-12)])
+def test_wide_2k_sampled(wg, oracle_lib, prec, eps):
+    """The 2048^2 / 999,936-visibility array workload at full size (the benchmark's launch
+    configuration): 256 sampled visibilities and 96 sampled pixels against the oracle."""
+    obs = S.wide_2k()
+    I = S.point_source_image(obs.npix_x, obs.npix_y, seed=0)
+    d = S.complex_normal((obs.nrows, obs.nchan), seed=1)
+    _, vis, img = run_pair(wg, obs, eps, prec, I, d)
+    rng = np.random.default_rng(0)
+    vsel = rng.choice(obs.nvis, 256, replace=False)
+    psel = rng.choice(obs.npix_x * obs.npix_y, 96, replace=False)
+    rv = oracle_lib.degrid(obs.uvw, obs.freq, I, obs.pixsize_x, obs.pixsize_y, vis_index=vsel)
+    ri = oracle_lib.grid(obs.uvw, obs.freq, d, obs.npix_x, obs.npix_y, obs.pixsize_x,
+                         obs.pixsize_y, pixel_index=psel)
+    assert oracle_lib.rel_l2(vis.reshape(-1)[vsel], rv) <= eps
+    assert oracle_lib.rel_l2(img.reshape(-1)[psel], ri) <= eps
+
+
+def test_unequal_axes_and_pixel_sizes(wg, oracle_lib):
+    obs = S.random_uvw_observation(500, 2, 32, 160, 12.0, seed=13)
+    obs.pixsize_y *= 0.7
+    I = S.gaussian_image(32, 160, seed=8)
+    d = S.complex_normal((500, 2), seed=9)
+    _, vis, img = run_pair(wg, obs, 1e-9, "f64", I, d)
+    rv, ri = oracle_pair(oracle_lib, obs, I, d)
+    assert oracle_lib.rel_l2(vis, rv) <= 1e-9 and oracle_lib.rel_l2(img, ri) <= 1e-9
+
+
+def test_degenerate_inputs(wg, oracle_lib):
+    # a single visibility, all w = 0, minimum image size
+    obs = S.random_uvw_observation(1, 1, 32, 32, 10.0, seed=15, wfrac=0.0)
+    I = S.gaussian_image(32, 32, seed=9)
+    d = S.complex_normal((1, 1), seed=10)
+    _, vis, img = run_pair(wg, obs, 1e-10, "f64", I, d)
+    rv, ri = oracle_pair(oracle_lib, obs, I, d)
+    assert oracle_lib.rel_l2(vis, rv) <= 1e-10 and oracle_lib.rel_l2(img, ri) <= 1e-10
+    # everything masked: zeros out, in both directions
+    obs = S.random_uvw_observation(50, 2, 64, 64, 10.0, seed=16)
+    mask = np.zeros((50, 2), np.uint8)
+    plan, vis, img = run_pair(wg, obs, 1e-5, "f32", S.gaussian_image(64, 64), S.complex_normal((50, 2)),
+                              mask=mask)
+    assert plan.info["nvis"] == 0 and not vis.any() and not img.any()
+    # no rows at all
+    empty = S.Observation(np.zeros((0, 3)), np.array([1e9]), 64, 64, 1e-3, 1e-3)
+    plan, vis, img = run_pair(wg, empty, 1e-5, "f32", S.gaussian_image(64, 64),
+                              np.zeros((0, 1), np.complex64))
+    assert vis.shape == (0, 1) and not img.any()
+
+
+def test_invalid_arguments_raise(wg):
+    obs = S.random_uvw_observation(10, 1, 64, 64, 10.0, seed=17)
+    for bad in (dict(epsilon=1e-13), dict(precision="f32", epsilon=5e-6), dict(npix_x=63)):
+        kw = dict(uvw=obs.uvw, freq=obs.freq, npix_x=64, npix_y=64, pixsize_x=obs.pixsize_x,
+                  pixsize_y=obs.pixsize_y, epsilon=1e-5, precision="f64")
+        kw.update(bad)
+        with pytest.raises(wg.WgridError):
+            wg.Plan(**kw)
+    with pytest.raises(wg.WgridError):
+        wg.Plan(obs.uvw, -obs.freq, 64, 64, obs.pixsize_x, obs.pixsize_y, 1e-5)
+
+
+def test_degrid_is_deterministic_and_oneshot_matches_plan(wg):
+    obs = S.random_uvw_observation(900, 4, 128, 128, 20.0, seed=21)
+    I = _cu(S.gaussian_image(128, 128, seed=3).astype(np.float32))
+    d = _cu(S.complex_normal((900, 4), seed=4).astype(np.complex64))
+    plan = wg.Plan(obs.uvw, obs.freq, 128, 128, obs.pixsize_x, obs.pixsize_y, 1e-4, "f32")
+    a, b = plan.degrid(I), plan.degrid(I)
+    assert torch.equal(a, b)
+    one = wg.dirty2ms(obs.uvw, obs.freq, I, pixsize_x=obs.pixsize_x, pixsize_y=obs.pixsize_y,
+                      epsilon=1e-4)
+    assert torch.equal(a, one)
+    g1 = plan.grid(d)
+    g2 = wg.ms2dirty(obs.uvw, obs.freq, d, npix_x=128, npix_y=128, pixsize_x=obs.pixsize_x,
+                     pixsize_y=obs.pixsize_y, epsilon=1e-4)
+    assert torch.allclose(g1, g2, rtol=0, atol=1e-5 * g1.abs().max().item())
+
+
+def test_host_inputs_are_accepted(wg):
+    """Host (numpy / CPU tensor) inputs go through the same C ABI after a device copy."""
+    obs = S.random_uvw_observation(300, 2, 64, 64, 20.0, seed=23)
+    I = S.gaussian_image(64, 64, seed=3)
+    plan = wg.Plan(obs.uvw, obs.freq, 64, 64, obs.pixsize_x, obs.pixsize_y, 1e-10, "f64")
+    a = plan.degrid(I).cpu()
+    b = plan.degrid(_cu(I)).cpu()
+    assert torch.equal(a, b)
