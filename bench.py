@@ -1,0 +1,423 @@
+#!/usr/bin/env python3
+"""Benchmark: visibilities/sec for degrid and grid at eps = 1e-5 (FP32) and 1e-12 (FP64).
+
+Workload (default ``wide_2k``): 2048^2 image at 20 arcsec, 999,936 visibilities from a
+64-antenna earth-rotation synthesis (2016 baselines x 62 time steps x 8 channels in
+0.9-1.7 GHz), point-source image (1% of pixels, log-normal flux), complex N(0, 1) data.
+
+One step = the four operator applications on that input: degrid + grid at eps = 1e-5 in
+FP32 and degrid + grid at eps = 1e-12 in FP64, each on a resident plan (index built once,
+outside the timed region).  ``value`` = 4 * nvis / step time.  The L2 cache is flushed
+between steps (256 MiB write), steps are timed with CUDA events on the launching stream,
+nvidia-smi clocks are sampled during the timed region.
+
+``--impl reference`` times the FP64 direct-sum oracle on the host cores on a bounded sample
+of the same workload (the reference arm); without it the oracle is timed once as the
+``cpu_baseline`` (rank 0, N = 1 only).  Under torchrun (N > 1) every rank runs an
+independent replica (the path is "replicas only"), weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "visibilities/sec for degrid and grid on 1 GB300 at eps=1e-5 (FP32) and 1e-12 (FP64)"
+MODES = (("f32", 1e-5), ("f64", 1e-12))
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="wgrid", choices=["wgrid", "reference"])
+    ap.add_argument("--workload", default="wide_2k")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--oracle-seconds", type=float, default=12.0)
+    ap.add_argument("--only", default=None,
+                    help="profiling aid: run only one call per step, e.g. f64:grid or f32:degrid")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons, power = [], None, set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1])); smax = float(parts[2]); power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+# ------------------------------------------------------------------------------------------
+# oracle (CPU) timing on a bounded sample
+# ------------------------------------------------------------------------------------------
+def oracle_rate(obs, I, d, seconds):
+    """Direct-sum terms per second of the oracle on this host, measured on a bounded sample:
+    degrid of a few visibilities (each a sum over all pixels) and grid of a few pixels (each
+    a sum over all visibilities).  Returns (vis_per_s, cores, sample description)."""
+    from oracle import direct
+    direct.build()
+    rng = np.random.default_rng(0)
+    npix = obs.npix_x * obs.npix_y
+    nnz = int(np.count_nonzero(I))     # the oracle skips zero pixels in degrid
+    # calibrate: one visibility
+    t0 = time.perf_counter()
+    direct.degrid(obs.uvw, obs.freq, I, obs.pixsize_x, obs.pixsize_y, vis_index=np.array([0]), nthreads=1)
+    t1 = time.perf_counter() - t0
+    cores = direct.threads_used(0)
+    nv = int(max(cores, min(200000, 0.5 * seconds / max(t1, 1e-9) * cores)))
+    vsel = rng.choice(obs.nvis, size=min(nv, obs.nvis), replace=False)
+    t0 = time.perf_counter()
+    direct.degrid(obs.uvw, obs.freq, I, obs.pixsize_x, obs.pixsize_y, vis_index=vsel)
+    td = time.perf_counter() - t0
+    degrid_vps = len(vsel) / td                      # visibilities degridded per second
+    # grid: one pixel costs nvis terms
+    t0 = time.perf_counter()
+    direct.grid(obs.uvw, obs.freq, d, obs.npix_x, obs.npix_y, obs.pixsize_x, obs.pixsize_y,
+                pixel_index=np.array([0]), nthreads=1)
+    t1 = time.perf_counter() - t0
+    npx = int(max(cores, min(npix, 0.5 * seconds / max(t1, 1e-9) * cores)))
+    psel = rng.choice(npix, size=npx, replace=False)
+    t0 = time.perf_counter()
+    direct.grid(obs.uvw, obs.freq, d, obs.npix_x, obs.npix_y, obs.pixsize_x, obs.pixsize_y, pixel_index=psel)
+    tg = time.perf_counter() - t0
+    grid_vps = obs.nvis / (tg * npix / len(psel))    # full image takes npix/len(psel) x longer
+    # one step = degrid + grid in each of the two modes (the oracle is FP64 in both)
+    step_s = 2 * (obs.nvis / degrid_vps + obs.nvis / grid_vps)
+    sample = (f"degrid of {len(vsel)} sampled visibilities against all {nnz} nonzero pixels "
+              f"({td:.1f} s) and grid of {len(psel)} sampled pixels over all {obs.nvis} "
+              f"visibilities ({tg:.1f} s), extrapolated to the full workload")
+    return 4 * obs.nvis / step_s, cores, sample, step_s
+
+
+def make_inputs(workload):
+    from paper_2010_10122_gb300 import synthetic as S
+    obs = S.WORKLOADS[workload]()
+    I = S.point_source_image(obs.npix_x, obs.npix_y, seed=0)
+    d = S.complex_normal((obs.nrows, obs.nchan), seed=1)
+    return obs, I, d
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    obs, I, d = make_inputs(args.workload)
+    per_step = max(2.0, args.oracle_seconds / max(1, args.steps + args.warmup))
+    rates = []
+    cores = sample = None
+    for i in range(args.warmup + args.steps):
+        vps, cores, sample, _ = oracle_rate(obs, I, d, per_step)
+        if i >= args.warmup:
+            rates.append(vps)
+    value = statistics.median(rates)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "vis/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 4 * obs.nvis / value * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "nvis": obs.nvis,
+                       "npix": [obs.npix_x, obs.npix_y], "modes": ["f32 eps=1e-5", "f64 eps=1e-12"]},
+            "cpu_baseline": {"value": value, "unit": "vis/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "vis/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------
+def algorithmic_flops_per_vis(alpha):
+    """FLOPs a (de)gridding kernel must do per visibility: alpha^3 complex-by-real
+    multiply-adds over the alpha planes x alpha x alpha cells (4 flops each), plus 3 alpha
+    kernel values by Horner of degree alpha + 3 (2 flops per step)."""
+    return 4 * alpha ** 3 + 3 * alpha * 2 * (alpha + 3)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2010_10122_gb300 import _build
+    if rank == 0 or ws == 1:
+        _build.build()
+    if ws > 1:
+        dist.barrier()
+    import paper_2010_10122_gb300 as wg
+
+    obs, I, d = make_inputs(args.workload)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    plans, dins, vins, vouts, gouts = {}, {}, {}, {}, {}
+    for prec, eps in MODES:
+        rdt, cdt = (torch.float32, torch.complex64) if prec == "f32" else (torch.float64, torch.complex128)
+        plans[prec] = wg.Plan(obs.uvw, obs.freq, obs.npix_x, obs.npix_y, obs.pixsize_x, obs.pixsize_y,
+                              eps, prec, device=dev)
+        dins[prec] = torch.from_numpy(I).to(dev, rdt)
+        vins[prec] = torch.from_numpy(d).to(dev, cdt)
+        vouts[prec] = torch.empty((obs.nrows, obs.nchan), dtype=cdt, device=dev)
+        gouts[prec] = torch.empty((obs.npix_x, obs.npix_y), dtype=rdt, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    per_call = {}
+
+    only = tuple(args.only.split(":")) if args.only else None
+
+    def step(with_stats=False):
+        for prec, _ in MODES:
+            p = plans[prec]
+            if only is None or only == (prec, "degrid"):
+                r1 = p.degrid(dins[prec], out=vouts[prec], stats=with_stats)
+                if with_stats:
+                    per_call.setdefault((prec, "degrid"), []).append(r1[1])
+            if only is None or only == (prec, "grid"):
+                r2 = p.grid(vins[prec], out=gouts[prec], stats=with_stats)
+                if with_stats:
+                    per_call.setdefault((prec, "grid"), []).append(r2[1])
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: per-step events, L2 flush between steps -----------------------------
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    clk = clocks.stop()
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = ws * 4 * obs.nvis / (ms_per_step * 1e-3)
+
+    # ---- per-call / per-stage breakdown (events inside the library, stage by stage) --------
+    for _ in range(max(2, args.steps // 2)):
+        flush.fill_(1)
+        step(with_stats=True)
+    torch.cuda.synchronize()
+    if only is not None:
+        st = per_call[only]
+        if rank == 0:
+            print(json.dumps({"only": args.only, "workload": args.workload,
+                              "ms_per_call": ms_per_step, "stats": st[-1],
+                              "plan": plans[only[0]].info}), flush=True)
+        for p in plans.values():
+            p.close()
+        return 0
+    modes = {}
+    launches = 0
+    for prec, eps in MODES:
+        info = plans[prec].info
+        m = {"eps": eps, "alpha": info["alpha"], "sigma": info["sigma"],
+             "grid": [info["nu"], info["nv"]], "nw": info["nw"], "batch": info["batch"]}
+        for direction in ("degrid", "grid"):
+            sts = per_call[(prec, direction)]
+            med = {k: statistics.median(s[k] for s in sts) for k in
+                   ("ms_total", "ms_prep", "ms_screen", "ms_fft", "ms_grid", "ms_accum")}
+            m[direction] = {"vis_per_s": obs.nvis / (med["ms_total"] * 1e-3),
+                            **{k: round(v, 4) for k, v in med.items()}}
+            launches += sts[-1]["n_kernels"]
+        modes[f"{prec}_eps{eps:g}"] = m
+    f32 = modes["f32_eps1e-05"]; f64 = modes["f64_eps1e-12"]
+    t32 = f32["degrid"]["ms_total"] + f32["grid"]["ms_total"]
+    t64 = f64["degrid"]["ms_total"] + f64["grid"]["ms_total"]
+
+    # ---- roofline of the dominant library kernel ----------------------------------------------
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    stage_ms = {}
+    for prec, _ in MODES:
+        k = f"{prec}_eps{dict(MODES)[prec]:g}"
+        for direction in ("degrid", "grid"):
+            s = modes[k][direction]
+            stage_ms[(prec, direction, "gridding")] = s["ms_grid"]
+            stage_ms[(prec, direction, "screen" if direction == "degrid" else "accumulate")] = (
+                s["ms_screen"] if direction == "degrid" else s["ms_accum"])
+    dom = max(stage_ms, key=stage_ms.get)
+    prec_d, dir_d, stage_d = dom
+    info_d = plans[prec_d].info
+    roof = None
+    if stage_d == "gridding" and prec_d == "f64":
+        flops = algorithmic_flops_per_vis(info_d["alpha"]) * plans[prec_d].info["nvis"]
+        peak = 1.25e12   # FP64 FMA pipe: nominal GB300 rate (152 SMs x 2 FMA/clk x 2 x 2.07 GHz)
+        ach = flops / (stage_ms[dom] * 1e-3)
+        roof = {"bound": "alu", "kernel": f"k_{dir_d}<double,16>", "achieved": ach / 1e12,
+                "peak": peak / 1e12, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                "peak_source": "nominal FP64 FMA rate (unit counts x clock); probe measured 1.19"}
+    else:
+        # plane-traffic kernels: bytes the stage must move per batch of planes
+        b = 8 if prec_d == "f32" else 16
+        cells = info_d["nu"] * info_d["nv"] * info_d["nw"]
+        npix = obs.npix_x * obs.npix_y
+        if stage_d == "screen":
+            byts = cells * b + npix * (16 if prec_d == "f32" else 32)
+        elif stage_d == "accumulate":
+            byts = info_d["nw"] * npix * b + npix * 8 * 2
+        else:
+            byts = cells * b
+        ach = byts / (stage_ms[dom] * 1e-3)
+        roof = {"bound": "hbm", "kernel": f"{stage_d} ({prec_d}, {dir_d})", "achieved": ach / 1e9,
+                "peak": hbm_peak, "unit": "GB/s", "frac": ach / 1e9 / hbm_peak, "traffic": None}
+
+    # ---- end to end: host buffers, copies inside the timed region ------------------------------
+    e2e = None
+    if not args.no_e2e:
+        h_in = {}
+        for prec, _ in MODES:
+            h_in[prec] = (dins[prec].cpu().pin_memory(), vins[prec].cpu().pin_memory())
+        h_out = {prec: (torch.empty(vouts[prec].shape, dtype=vouts[prec].dtype).pin_memory(),
+                        torch.empty(gouts[prec].shape, dtype=gouts[prec].dtype).pin_memory())
+                 for prec, _ in MODES}
+        bi = sum(a.numel() * a.element_size() + b_.numel() * b_.element_size() for a, b_ in h_in.values())
+        bo = sum(a.numel() * a.element_size() + b_.numel() * b_.element_size() for a, b_ in h_out.values())
+
+        def e2e_step():
+            for prec, _ in MODES:
+                di = h_in[prec][0].to(dev, non_blocking=True)
+                vi = h_in[prec][1].to(dev, non_blocking=True)
+                vo = plans[prec].degrid(di)
+                go = plans[prec].grid(vi)
+                h_out[prec][0].copy_(vo, non_blocking=True)
+                h_out[prec][1].copy_(go, non_blocking=True)
+        for _ in range(args.warmup):
+            e2e_step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0.record(stream)
+            e2e_step()
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        e2e = {"value": ws * 4 * obs.nvis / (tot / args.steps * 1e-3), "unit": "vis/s",
+               "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        vps, cores, sample, _ = oracle_rate(obs, I, d, args.oracle_seconds)
+        cpu = {"value": vps, "unit": "vis/s", "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "vis/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": args.workload, "nvis": obs.nvis,
+                           "npix": [obs.npix_x, obs.npix_y], "pixsize_arcsec": obs.pixsize_x / S_ARCSEC(),
+                           "uv_scale": obs.uv_scale,
+                           "step": "degrid+grid at eps=1e-5 f32 and at eps=1e-12 f64, resident plans",
+                           "parallelism": f"replicas{ws}" if ws > 1 else "single",
+                           "l2": "flushed between steps (256 MiB write)"},
+                "modes": modes, "fp32_vs_fp64_speedup": t64 / t32,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches * args.steps, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    for p in plans.values():
+        p.close()
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def S_ARCSEC():
+    from paper_2010_10122_gb300 import synthetic as S
+    return S.ARCSEC
+
+
+if __name__ == "__main__":
+    sys.exit(main())

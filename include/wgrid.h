@@ -60,9 +60,9 @@ enum wg_precision { WG_F32 = 0, WG_F64 = 1 };
 
 /* Opaque plan: geometry, kernel choice and the on-device visibility index for one set of
  * (uvw, freq, mask, image geometry, epsilon, precision).  Reusable for any number of
- * degrid / grid calls; calls on one plan may not run concurrently with each other on
- * different streams (they share the plan's scratch state only through the workspace
- * they allocate per call, so concurrent calls are safe if each uses its own stream). */
+ * degrid / grid calls.  The plan's device data is read-only after creation and every call
+ * allocates its own workspace, so calls on one plan may run concurrently on different
+ * streams (host threads included); destroy the plan only after its calls have finished. */
 typedef struct wg_plan wg_plan;
 
 /* Options for wg_plan_create (zero-initialise, then set what you need). */
@@ -93,6 +93,8 @@ typedef struct wg_stats {
   int64_t n_batches;   /* plane batches processed */
   int64_t n_planes;    /* w-planes processed */
   size_t workspace_bytes; /* device workspace used by the call */
+  int64_t n_kernels;   /* library kernels launched by the call (cuFFT's own not counted) */
+  int64_t n_fft_calls; /* cuFFT executions */
 } wg_stats;
 
 /* Plan parameters chosen by the planner (Sec. 4.1, App. A). */

@@ -534,6 +534,8 @@ static int degrid_impl(wg_plan* p, const R* dirty, const R* wgt, typename C2<R>:
     std::memset(stats, 0, sizeof(*stats));
     tm.finish(stats);
     stats->n_batches = nbatches; stats->n_planes = g.nw; stats->workspace_bytes = w.total;
+    stats->n_kernels = 1 + 2 * nbatches;   // prep, then screen + degrid per batch
+    stats->n_fft_calls = nbatches;
   }
   return WG_OK;
 }
@@ -591,6 +593,8 @@ static int grid_impl(wg_plan* p, const typename C2<R>::T* vis, const R* wgt, R* 
     std::memset(stats, 0, sizeof(*stats));
     tm.finish(stats);
     stats->n_batches = nbatches; stats->n_planes = g.nw; stats->workspace_bytes = w.total;
+    stats->n_kernels = 1 + 2 * nbatches;   // prep, then grid + accumulate per batch
+    stats->n_fft_calls = nbatches;
   }
   return WG_OK;
 }

@@ -111,6 +111,12 @@ def wide_2k(seed=0) -> Observation:
     return array_observation(64, 62, 8, 2048, 20 * ARCSEC, seed=seed, name="wide_2k")
 
 
+def wide_1k(seed=0) -> Observation:
+    """Quarter-size variant of wide_2k (1024^2 at 40 arcsec, 64 antennas x 31 x 8 channels),
+    small enough for profiler captures that replay each kernel many times."""
+    return array_observation(64, 31, 8, 1024, 40 * ARCSEC, seed=seed, name="wide_1k")
+
+
 def wide_8k(seed=0) -> Observation:
     return array_observation(128, 193, 64, 8192, 4 * ARCSEC, seed=seed, max_rows=1_562_500,
                              name="wide_8k")
@@ -120,7 +126,8 @@ def diff_4k(seed=0) -> Observation:
     return array_observation(64, 310, 16, 4096, 4 * ARCSEC, seed=seed, name="diff_4k")
 
 
-WORKLOADS = {"tiny": tiny, "wide_2k": wide_2k, "wide_8k": wide_8k, "diff_4k": diff_4k}
+WORKLOADS = {"tiny": tiny, "wide_1k": wide_1k, "wide_2k": wide_2k, "wide_8k": wide_8k,
+             "diff_4k": diff_4k}
 
 
 def random_uvw_observation(nrows, nchan, npix_x, npix_y, fov_deg, seed=0, wfrac=0.5,

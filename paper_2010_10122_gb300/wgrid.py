@@ -44,7 +44,8 @@ class Stats(ctypes.Structure):
                 ("ms_screen", ctypes.c_double), ("ms_fft", ctypes.c_double),
                 ("ms_grid", ctypes.c_double), ("ms_accum", ctypes.c_double),
                 ("n_batches", ctypes.c_int64), ("n_planes", ctypes.c_int64),
-                ("workspace_bytes", ctypes.c_size_t)]
+                ("workspace_bytes", ctypes.c_size_t), ("n_kernels", ctypes.c_int64),
+                ("n_fft_calls", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
