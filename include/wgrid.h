@@ -79,6 +79,9 @@ typedef struct wg_options {
   int force_alpha;         /* >0: only consider kernels with this support (tests) */
   double force_sigma;      /* >0: only consider this oversampling factor (tests) */
   int tile;                /* uv tile side in cells (16 or 32; 0 = automatic) */
+  int grid_variant;        /* gridding accumulation: 0 = automatic (shared-memory atomics for
+                              WG_F32, plane-owner warps for WG_F64), 1 = shared-memory atomics,
+                              2 = plane-owner warps (deterministic) */
 } wg_options;
 
 /* Per-call statistics (optional output).  Stage times are CUDA-event times measured on the
@@ -211,6 +214,12 @@ int wg_kernel_psi(int alpha, double beta, double mu, const double* k, double* ou
 int wg_plan_params(int64_t npix_x, int64_t npix_y, double pixsize_x, double pixsize_y,
                    double epsilon, int precision, const wg_options* opt, double umax,
                    double vmax, double wmin, double wmax, int64_t nvis, wg_plan_info* info);
+
+/* Planner calibration: time the batched 2-D cuFFT of `batch` n x n planes (C2C for WG_F32,
+ * Z2Z for WG_F64) on the current device, `reps` executions after one warm-up, and return the
+ * mean time per plane in milliseconds.  Allocates and frees its own device memory; synchronises
+ * the device.  Errors: WG_ERR_ARG, WG_ERR_OOM, WG_ERR_CUFFT, WG_ERR_CUDA. */
+int wg_fft_time(int64_t n, int precision, int64_t batch, int reps, double* ms_per_plane);
 
 /* Library version string. */
 const char* wg_version(void);

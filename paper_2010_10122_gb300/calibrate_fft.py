@@ -1,0 +1,59 @@
+"""Measure cuFFT plane-transform times for the planner's candidate grid sizes and write them
+to csrc/fft_table.inc (run on the target GPU; the library must be built).
+
+Candidates: n = 32 m for 4 <= m <= 512 with m 11-smooth (FFT-friendly multiples of the uv
+tile).  For each n the batched 2-D C2C (FP32) and Z2Z (FP64) transforms are timed through the
+library's wg_fft_time entry point with ~1-2 GiB of planes per batch.  The planner uses the
+table to pick, for each oversampling factor, the fastest size >= sigma * n and to price the
+FFT stage in its cost model (Sec. 4.1).
+
+usage: python -m paper_2010_10122_gb300.calibrate_fft [--max-n 16384] [--out PATH]
+"""
+import argparse
+import os
+import sys
+import time
+
+
+def smooth(m, primes=(2, 3, 5, 7, 11)):
+    for p in primes:
+        while m % p == 0:
+            m //= p
+    return m == 1
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--max-n", type=int, default=16384)
+    ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                                                  "csrc", "fft_table.inc"))
+    args = ap.parse_args()
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    from paper_2010_10122_gb300 import _build
+    _build.build()
+    import paper_2010_10122_gb300 as wg
+    import torch
+    rows = []
+    t0 = time.time()
+    for m in range(4, args.max_n // 32 + 1):
+        if not smooth(m):
+            continue
+        n = 32 * m
+        out = [n]
+        for prec, b in (("f32", 8), ("f64", 16)):
+            batch = max(1, min(64, int((1.5 * 2**30) // (n * n * b))))
+            reps = 3 if n * n * b * batch > 2**28 else 6
+            out.append(wg.fft_time(n, prec, batch=batch, reps=reps))
+        rows.append(out)
+        print(f"n={n:6d} c2c {out[1]*1e3:9.2f} us/plane  z2z {out[2]*1e3:10.2f} us/plane", flush=True)
+    dev = torch.cuda.get_device_name(0)
+    with open(args.out, "w") as f:
+        f.write(f"// cuFFT batched 2-D plane transform times on {dev}, measured by\n")
+        f.write("// paper_2010_10122_gb300/calibrate_fft.py: {n, ms per plane C2C, ms per plane Z2Z}\n")
+        for n, a, b in rows:
+            f.write(f"{{{n}, {a:.6g}, {b:.6g}}},\n")
+    print(f"wrote {len(rows)} sizes to {args.out} in {time.time() - t0:.0f} s")
+
+
+if __name__ == "__main__":
+    main()

@@ -256,19 +256,68 @@ int64_t good_size(int64_t n, int64_t mult) {
   return q * mult;
 }
 
-// Rough GB300 cost model (seconds), Sec. 4.1: FFT and plane traffic per w-plane plus the
-// per-visibility gridding work alpha^3.  Constants come from measured cuFFT C2C/Z2Z
-// plane times, the HBM copy rate and the FP32 / FP64 FMA and shared-atomic rates.
+// Measured cuFFT plane times on GB300 (batched 2-D C2C / Z2Z), written by calibrate_fft.py.
+struct FftRow {
+  int64_t n;
+  double ms32, ms64;
+};
+static const FftRow kFftTable[] = {
+#include "fft_table.inc"
+};
+static const size_t kFftRows = sizeof(kFftTable) / sizeof(kFftTable[0]);
+
+// Milliseconds of one n x n plane transform: the table value, else an n^2 log n extrapolation
+// from the largest measured size.
+static double fft_ms_square(int64_t n, int prec) {
+  for (size_t i = 0; i < kFftRows; ++i)
+    if (kFftTable[i].n == n) return prec ? kFftTable[i].ms64 : kFftTable[i].ms32;
+  const FftRow& L = kFftTable[kFftRows - 1];
+  double ref = prec ? L.ms64 : L.ms32;
+  double a = (double)n * n * std::log2((double)n * n), b = (double)L.n * L.n * std::log2((double)L.n * L.n);
+  return ref * a / b * 1.3;   // unmeasured sizes are priced a little higher
+}
+
+// Rectangular nu x nv plane: per-cell cost averaged over the two axis lengths.
+static double fft_ms(int64_t nu, int64_t nv, int prec) {
+  double cu = fft_ms_square(nu, prec) / ((double)nu * nu);
+  double cv = fft_ms_square(nv, prec) / ((double)nv * nv);
+  return 0.5 * (cu + cv) * (double)nu * nv;
+}
+
+// Grid-size candidates >= nmin: the next measured sizes (multiples of `mult`), or FFT-friendly
+// sizes beyond the table.
+static std::vector<int64_t> size_candidates(int64_t nmin, int64_t mult) {
+  std::vector<int64_t> c;
+  for (size_t i = 0; i < kFftRows && c.size() < 10; ++i)
+    if (kFftTable[i].n >= nmin && kFftTable[i].n % mult == 0) c.push_back(kFftTable[i].n);
+  if (c.empty()) c.push_back(good_size(nmin, mult));
+  return c;
+}
+
+// GB300 cost model (seconds), Sec. 4.1: per w-plane the FFT (measured) plus plane traffic
+// per cell and the w-screen phase per image pixel; per visibility the alpha^3 (de)gridding
+// work.  The per-cell / per-pixel / per-visibility constants are measured stage times of this
+// library on GB300 (2048^2 image, 1e6 visibilities) divided by the units processed.
 static double plan_cost(int prec, int64_t nu, int64_t nv, int64_t nw, int alpha, int64_t nvis,
                         int64_t npix) {
   double cells = (double)nu * nv;
-  double lg = std::log2(cells);
-  double k_fft = prec ? 9.2e-12 : 3.8e-13;        // s per cell * log2(cells) per plane
-  double k_cell = prec ? 7.0e-12 : 3.5e-12;       // s per cell per plane (screen, (de)grid traffic)
-  double k_pix = prec ? 3.4e-11 : 1.0e-12;        // s per image pixel per plane (phase)
-  double k_vis = prec ? 1.3e-11 : 2.0e-12;        // s per visibility per alpha^3
-  return nw * (cells * lg * k_fft + cells * k_cell + (double)npix * k_pix) +
+  double k_cell = prec ? 3.0e-12 : 2.5e-12;   // s per plane cell (screen / (de)grid traffic)
+  double k_pix = prec ? 6.0e-11 : 1.8e-12;    // s per image pixel per plane (screen phase)
+  double k_vis = prec ? 1.05e-11 : 5.0e-12;   // s per visibility per alpha^3
+  return nw * (1e-3 * fft_ms(nu, nv, prec) + cells * k_cell + (double)npix * k_pix) +
          (double)nvis * alpha * alpha * alpha * k_vis;
+}
+
+// Cheapest (nu, nv) for one plane among the candidates (FFT + traffic per cell).
+static void choose_grid(int64_t nmin_u, int64_t nmin_v, int prec, int64_t mult, int64_t* nu,
+                        int64_t* nv) {
+  double k_cell = prec ? 3.0e-12 : 2.5e-12;
+  double best = std::numeric_limits<double>::infinity();
+  for (int64_t a : size_candidates(nmin_u, mult))
+    for (int64_t b : size_candidates(nmin_v, mult)) {
+      double c = 1e-3 * fft_ms(a, b, prec) + k_cell * (double)a * b;
+      if (c < best) { best = c; *nu = a; *nv = b; }
+    }
 }
 
 int choose_plan(const PlanInput& in, PlanParams& out, char* err, int errlen) {
@@ -311,10 +360,12 @@ int choose_plan(const PlanInput& in, PlanParams& out, char* err, int errlen) {
     p.alpha = alpha; p.sigma = pick->sigma; p.beta = pick->beta; p.mu = pick->mu;
     p.eps_kernel = pick->eps;
     p.tile = tile;
-    // Sec. 2: N = ceil(sigma n), rounded up to an FFT-friendly multiple of the tile
+    // Sec. 2: N >= ceil(sigma n); among the FFT-friendly multiples of the tile above it the
+    // one with the cheapest measured plane transform
     int64_t minn = std::max<int64_t>(2 * alpha, 16);
-    p.nu = good_size(std::max<int64_t>((int64_t)std::ceil(p.sigma * in.nx), minn), tile);
-    p.nv = good_size(std::max<int64_t>((int64_t)std::ceil(p.sigma * in.ny), minn), tile);
+    choose_grid(std::max<int64_t>((int64_t)std::ceil(p.sigma * in.nx), minn),
+                std::max<int64_t>((int64_t)std::ceil(p.sigma * in.ny), minn), in.prec, tile,
+                &p.nu, &p.nv);
     p.ntu = p.nu / tile; p.ntv = p.nv / tile;
     p.nm1_min = nm1_min;
     if (in.do_w) {

@@ -337,6 +337,8 @@ int wg_plan_create(const double* uvw, const double* freq, int64_t nrows, int64_t
   g.psx = pixsize_x; g.psy = pixsize_y;
   g.w0 = pp.w0; g.dw = pp.dw; g.nshift = pp.nshift;
   g.w0_dw = pp.w0 / pp.dw;
+  g.grid_variant = p->opt.grid_variant;
+  if (g.grid_variant < 0 || g.grid_variant > 2) return set_error(WG_ERR_ARG, "grid_variant must be 0, 1 or 2");
   fill_coefs(p.get());
 
   int rc = WG_OK;
@@ -710,6 +712,44 @@ int wg_plan_params(int64_t npix_x, int64_t npix_y, double pixsize_x, double pixs
   info->ntiles = pp.ntu * pp.ntv; info->nvis = nvis;
   info->umax = umax; info->vmax = vmax; info->wmin = wmin; info->wmax = wmax;
   return WG_OK;
+}
+
+int wg_fft_time(int64_t n, int precision, int64_t batch, int reps, double* ms_per_plane) {
+  if (n < 2 || batch < 1 || reps < 1 || ms_per_plane == nullptr ||
+      (precision != WG_F32 && precision != WG_F64))
+    return set_error(WG_ERR_ARG, "bad arguments");
+  size_t bytes = (size_t)n * n * batch * cplx_bytes(precision);
+  cufftHandle h;
+  size_t ws = 0;
+  WG_TRY(make_fft(&h, precision, n, n, batch, &ws));
+  void *data = nullptr, *work = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = WG_OK;
+  do {
+    if ((rc = dev_alloc((unsigned char**)&data, bytes)) != WG_OK) break;
+    if (ws > 0 && (rc = dev_alloc((unsigned char**)&work, ws)) != WG_OK) break;
+    if (cudaMemset(data, 0, bytes) != cudaSuccess) { rc = set_error(WG_ERR_CUDA, "memset"); break; }
+    if (cufftSetWorkArea(h, work) != CUFFT_SUCCESS) { rc = set_error(WG_ERR_CUFFT, "work area"); break; }
+    cudaEventCreate(&e0); cudaEventCreate(&e1);
+    float ms = 0.f;
+    for (int r = 0; r <= reps; ++r) {
+      if (r == 1) cudaEventRecord(e0, 0);
+      cufftResult fr = precision ? cufftExecZ2Z(h, (cufftDoubleComplex*)data, (cufftDoubleComplex*)data, CUFFT_FORWARD)
+                                 : cufftExecC2C(h, (cufftComplex*)data, (cufftComplex*)data, CUFFT_FORWARD);
+      if (fr != CUFFT_SUCCESS) { rc = set_error(WG_ERR_CUFFT, "exec %d", (int)fr); break; }
+    }
+    if (rc != WG_OK) break;
+    cudaEventRecord(e1, 0);
+    if (cudaEventSynchronize(e1) != cudaSuccess) { rc = set_error(WG_ERR_CUDA, "sync"); break; }
+    cudaEventElapsedTime(&ms, e0, e1);
+    *ms_per_plane = ms / (double)(reps * batch);
+  } while (0);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (data) cudaFree(data);
+  if (work) cudaFree(work);
+  cufftDestroy(h);
+  return rc;
 }
 
 const char* wg_version(void) { return "wgrid-gb300 0.1 (sm_103a)"; }

@@ -38,6 +38,7 @@ struct Geom {
   double psx, psy;
   double w0, dw, nshift;
   double w0_dw;         // w0 / dw
+  int grid_variant;     // 0 automatic, 1 shared atomics, 2 plane-owner warps
 };
 
 // Kernel polynomial coefficients, layout [d][G] so lane j reads c[d * kMaxG + j].

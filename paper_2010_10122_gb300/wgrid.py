@@ -36,7 +36,7 @@ class Options(ctypes.Structure):
     _fields_ = [("do_wstacking", ctypes.c_int), ("w_shift", ctypes.c_int),
                 ("eps_safety", ctypes.c_double), ("max_workspace", ctypes.c_size_t),
                 ("force_alpha", ctypes.c_int), ("force_sigma", ctypes.c_double),
-                ("tile", ctypes.c_int)]
+                ("tile", ctypes.c_int), ("grid_variant", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -88,6 +88,7 @@ SIGNATURES = {
     "wg_kernel_psi": (_I, [_I, _D, _D, _VP, _VP, _I64]),
     "wg_plan_params": (_I, [_I64, _I64, _D, _D, _D, _I, ctypes.POINTER(Options), _D, _D, _D, _D,
                             _I64, ctypes.POINTER(PlanInfo)]),
+    "wg_fft_time": (_I, [_I64, _I, _I64, _I, ctypes.POINTER(_D)]),
     "wg_version": (ctypes.c_char_p, []),
 }
 
@@ -174,8 +175,8 @@ class Plan:
 
     def __init__(self, uvw, freq, npix_x, npix_y, pixsize_x, pixsize_y, epsilon,
                  precision="f32", mask=None, do_wstacking=True, w_shift=True, eps_safety=1.0,
-                 max_workspace=0, force_alpha=0, force_sigma=0.0, tile=0, stream=None,
-                 device=None):
+                 max_workspace=0, force_alpha=0, force_sigma=0.0, tile=0, grid_variant=0,
+                 stream=None, device=None):
         self._h = None
         dev = _device(device)
         self.device = dev
@@ -190,7 +191,7 @@ class Plan:
         opt = default_options(do_wstacking=int(bool(do_wstacking)), w_shift=int(bool(w_shift)),
                               eps_safety=float(eps_safety), max_workspace=int(max_workspace),
                               force_alpha=int(force_alpha), force_sigma=float(force_sigma),
-                              tile=int(tile))
+                              tile=int(tile), grid_variant=int(grid_variant))
         h = ctypes.c_void_p()
         with torch.cuda.device(dev):
             rc = lib().wg_plan_create(_ptr(uvw_t), _ptr(freq_t), self.nrows, self.nchan,
@@ -349,6 +350,13 @@ def plan_params(npix_x, npix_y, pixsize_x, pixsize_y, epsilon, precision="f32", 
                                 float(epsilon), _prec(precision), ctypes.byref(o), float(umax),
                                 float(vmax), float(wmin), float(wmax), int(nvis), ctypes.byref(inf)))
     return inf.as_dict()
+
+
+def fft_time(n, precision="f32", batch=1, reps=3) -> float:
+    """Milliseconds per plane of the batched n x n cuFFT transform (planner calibration)."""
+    ms = ctypes.c_double()
+    _check(lib().wg_fft_time(int(n), _prec(precision), int(batch), int(reps), ctypes.byref(ms)))
+    return ms.value
 
 
 def version() -> str:

@@ -89,11 +89,12 @@ def test_planner_follows_sec2_definitions(wg, w_shift, prec, eps):
     # chosen kernel meets epsilon and is the smallest such sigma for its alpha (Sec. 4.1)
     rows = [r for r in wg.kernel_table() if r[0] == alpha and r[2] <= eps]
     assert info["eps_kernel"] <= eps and sigma == min(r[1] for r in rows)
-    # N = ceil(sigma n), rounded up to an FFT-friendly multiple of the tile
+    # N >= ceil(sigma n), an FFT-friendly (11-smooth) multiple of the tile, and not much above
     for n, N in ((a["npix_x"], info["nu"]), (a["npix_y"], info["nv"])):
         assert N >= math.ceil(sigma * n) and N % info["tile"] == 0
+        assert N <= 1.25 * math.ceil(sigma * n) + 64
         q = N // info["tile"]
-        for pr in (2, 3, 5, 7):
+        for pr in (2, 3, 5, 7, 11):
             while q % pr == 0:
                 q //= pr
         assert q == 1
