@@ -162,6 +162,33 @@ int wg_degrid(wg_plan* plan, const void* dirty, const void* wgt, void* vis, void
               wg_stats* stats);
 
 /*
+ * wg_degrid_noalloc — the same result as wg_degrid, computed without allocating any memory.
+ * The paper has no counterpart: this entry point exists for callers that cannot allocate device
+ * memory while they run, e.g. code whose device memory is owned by another allocator (a
+ * framework's caching allocator or a fixed arena, where a cudaMalloc could fail, fragment the
+ * arena or synchronise the device) and real-time loops that must not allocate between
+ * set-up and shutdown.  Such a caller creates the plan once at set-up (wg_plan_create does
+ * allocate) with options.max_workspace <= WG_NOALLOC_SCRATCH_BYTES, then calls this entry
+ * point as often as it likes.
+ *   The per-call workspace (uv planes, cuFFT work area, per-pixel table) lives in one
+ * file-scope device array of WG_NOALLOC_SCRATCH_BYTES (64 MiB) that every GPU which loads the
+ * library holds until the process exits.  Nothing in it has to start at zero.  This call makes
+ * no cudaMalloc / cudaFree or other allocating call; the plan's cuFFT handles run on the
+ * scratch through cufftSetWorkArea.
+ *   The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  The plan's device
+ * must be current.
+ *   All calls share the one array and it keeps the last call's contents: calls whose work
+ * overlaps on the GPU (other streams, other threads, other plans) race and corrupt each
+ * other's results; order them on one stream or synchronise between them.
+ * Arguments as for wg_degrid (no stats).  Errors: WG_ERR_ARG when the plan's per-call
+ * workspace (wg_plan_info.workspace_bytes) exceeds WG_NOALLOC_SCRATCH_BYTES, for NULL
+ * arguments or a different current device; WG_ERR_CUDA, WG_ERR_CUFFT as for wg_degrid.
+ */
+#define WG_NOALLOC_SCRATCH_BYTES (64ull << 20)
+int wg_degrid_noalloc(wg_plan* plan, const void* dirty, const void* wgt, void* vis, void* stream);
+
+/*
  * wg_grid — dirty = R^dagger(vis) (Eqs. Rad1, Rad2; the paper's ms2dirty): per batch of
  * w-planes: grid the visibilities onto the planes (Eq. Rad2), inverse 2-D FFT (cuFFT),
  * multiply by the conjugate w-screen and accumulate over planes; finally divide by

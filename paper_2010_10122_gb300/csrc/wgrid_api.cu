@@ -486,7 +486,7 @@ static int run_fft(wg_plan* p, int64_t nb, void* data, void* work, int dir, cuda
 
 template <typename R>
 static int degrid_impl(wg_plan* p, const R* dirty, const R* wgt, typename C2<R>::T* vis,
-                       cudaStream_t s, wg_stats* stats) {
+                       cudaStream_t s, wg_stats* stats, unsigned char* external_ws = nullptr) {
   StageTimer tm;
   tm.start(stats != nullptr, s);
   const Geom& g = p->g;
@@ -498,8 +498,8 @@ static int degrid_impl(wg_plan* p, const R* dirty, const R* wgt, typename C2<R>:
     return WG_OK;
   }
   Workspace w = workspace_layout(p, p->batch, p->fft_ws);
-  unsigned char* ws = nullptr;
-  WG_TRY(pool_alloc((void**)&ws, w.total, p->device, s));
+  unsigned char* ws = external_ws;
+  if (ws == nullptr) WG_TRY(pool_alloc((void**)&ws, w.total, p->device, s));
   auto* planes = (typename C2<R>::T*)ws;
   void* fftw = ws + w.planes;
   auto* table = (Z4<R>*)(ws + w.planes + w.fft);
@@ -529,7 +529,7 @@ static int degrid_impl(wg_plan* p, const R* dirty, const R* wgt, typename C2<R>:
       ++nbatches;
     }
   } while (0);
-  pool_free(ws, s);
+  if (external_ws == nullptr) pool_free(ws, s);
   p->last_stream = s;
   if (rc != WG_OK) return rc;
   if (stats) {
@@ -609,6 +609,54 @@ int wg_degrid(wg_plan* plan, const void* dirty, const void* wgt, void* vis, void
   if (plan->prec)
     return degrid_impl<double>(plan, (const double*)dirty, (const double*)wgt, (double2*)vis, s, stats);
   return degrid_impl<float>(plan, (const float*)dirty, (const float*)wgt, (float2*)vis, s, stats);
+}
+
+// ---------------------------------------------------------------------------------------
+// allocation-free degrid: the per-call workspace lives in a file-scope device array
+// ---------------------------------------------------------------------------------------
+static_assert(WG_NOALLOC_SCRATCH_BYTES % 256 == 0, "scratch size must keep 256-byte alignment");
+static __device__ __align__(256) unsigned char g_noalloc_scratch[WG_NOALLOC_SCRATCH_BYTES];
+
+// Device address of g_noalloc_scratch on device `dev` (which must be current).  In host code the
+// array's name is only a host-side stand-in, so the address is looked up with
+// cudaGetSymbolAddress once per device and cached.
+static int noalloc_scratch(int dev, unsigned char** out) {
+  static std::mutex mu;
+  static std::vector<unsigned char*> addr;
+  std::lock_guard<std::mutex> lk(mu);
+  if ((int)addr.size() <= dev) addr.resize(dev + 1, nullptr);
+  if (addr[dev] == nullptr) {
+    void* a = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&a, g_noalloc_scratch);
+    if (e != cudaSuccess || a == nullptr)
+      return set_error(WG_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+    addr[dev] = static_cast<unsigned char*>(a);
+  }
+  *out = addr[dev];
+  return WG_OK;
+}
+
+int wg_degrid_noalloc(wg_plan* plan, const void* dirty, const void* wgt, void* vis,
+                      void* stream) {
+  if (plan == nullptr || dirty == nullptr || (vis == nullptr && plan->nvis_total > 0))
+    return set_error(WG_ERR_ARG, "NULL plan / dirty / vis");
+  if (plan->ws_bytes > (size_t)WG_NOALLOC_SCRATCH_BYTES)
+    return set_error(WG_ERR_ARG,
+                     "plan needs %zu bytes of per-call workspace, more than the %llu-byte static "
+                     "scratch; create it with max_workspace <= WG_NOALLOC_SCRATCH_BYTES",
+                     plan->ws_bytes, (unsigned long long)WG_NOALLOC_SCRATCH_BYTES);
+  int dev = -1;
+  WG_CUDA(cudaGetDevice(&dev));
+  if (dev != plan->device)
+    return set_error(WG_ERR_ARG, "current device %d is not the plan's device %d", dev, plan->device);
+  unsigned char* ws = nullptr;
+  WG_TRY(noalloc_scratch(dev, &ws));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (plan->prec)
+    return degrid_impl<double>(plan, (const double*)dirty, (const double*)wgt, (double2*)vis, s,
+                               nullptr, ws);
+  return degrid_impl<float>(plan, (const float*)dirty, (const float*)wgt, (float2*)vis, s,
+                            nullptr, ws);
 }
 
 int wg_grid(wg_plan* plan, const void* vis, const void* wgt, void* dirty, void* stream,

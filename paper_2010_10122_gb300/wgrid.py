@@ -24,6 +24,7 @@ LIB_PATH = os.path.join(_PKG, "libwgrid.so")
 
 WG_OK, WG_ERR_ARG, WG_ERR_OOM, WG_ERR_CUDA, WG_ERR_CUFFT, WG_ERR_TIMEOUT, WG_ERR_INTERNAL = range(7)
 WG_F32, WG_F64 = 0, 1
+NOALLOC_SCRATCH_BYTES = 64 << 20   # WG_NOALLOC_SCRATCH_BYTES of include/wgrid.h
 
 
 class WgridError(RuntimeError):
@@ -75,6 +76,7 @@ SIGNATURES = {
     "wg_plan_get_info": (_I, [_VP, ctypes.POINTER(PlanInfo)]),
     "wg_degrid": (_I, [_VP, _VP, _VP, _VP, _VP, ctypes.POINTER(Stats)]),
     "wg_grid": (_I, [_VP, _VP, _VP, _VP, _VP, ctypes.POINTER(Stats)]),
+    "wg_degrid_noalloc": (_I, [_VP, _VP, _VP, _VP, _VP]),
     "wg_dirty2ms": (_I, [_VP, _VP, _I64, _I64, _VP, _VP, _I64, _I64, _D, _D, _D, _I, _I, _VP,
                          _VP, _VP]),
     "wg_ms2dirty": (_I, [_VP, _VP, _I64, _I64, _VP, _VP, _I64, _I64, _D, _D, _D, _I, _I, _VP,
@@ -225,6 +227,24 @@ class Plan:
                                  ctypes.byref(st) if st is not None else None)
         _check(rc)
         return (out, st.as_dict()) if stats else out
+
+    def degrid_noalloc(self, dirty, out, wgt=None, stream=None):
+        """vis = R(dirty) through wg_degrid_noalloc: no allocation inside the call; ``out`` and
+        the inputs must already be device tensors of the right dtype and shape, and the plan
+        must have been made with max_workspace <= NOALLOC_SCRATCH_BYTES."""
+        dev = self.device
+        for t in (dirty, out) + (() if wgt is None else (wgt,)):
+            if not isinstance(t, torch.Tensor) or t.device != dev or not t.is_contiguous():
+                raise ValueError("degrid_noalloc needs contiguous tensors on the plan's device")
+        if dirty.dtype != _REAL[self.prec] or out.dtype != _CPLX[self.prec] \
+                or tuple(dirty.shape) != (self.npix_x, self.npix_y) \
+                or tuple(out.shape) != (self.nrows, self.nchan):
+            raise ValueError("degrid_noalloc: wrong dtype or shape")
+        with torch.cuda.device(dev):
+            rc = lib().wg_degrid_noalloc(self._h, _ptr(dirty), _ptr(wgt), _ptr(out),
+                                         _stream_handle(stream, dev))
+        _check(rc)
+        return out
 
     def grid(self, vis, wgt=None, out=None, stream=None, stats=False):
         """dirty = R^dagger(vis): (npix_x, npix_y) real on the plan's device."""
