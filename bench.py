@@ -52,10 +52,8 @@ def parse():
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_2010_10122_gb300 import replicas
+    return replicas.world()
 
 
 # ------------------------------------------------------------------------------------------
@@ -270,11 +268,8 @@ def main():
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     clk = clocks.stop()
-    total_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    from paper_2010_10122_gb300 import replicas
+    total_ms = replicas.max_over_ranks(sum(step_ms), device=dev)
     ms_per_step = total_ms / args.steps
     value = ws * 4 * obs.nvis / (ms_per_step * 1e-3)
 

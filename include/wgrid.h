@@ -73,7 +73,8 @@ typedef struct wg_options {
                               Delta w = 1 / (2 sigma max|n - 1|) (Sec. 2). Default used by
                               wg_default_options: 1 */
   double eps_safety;       /* kernels are chosen with table epsilon <= epsilon * eps_safety
-                              (default 1.0) */
+                              (default 0.8: the table value is a 1-D error, the gridding
+                              combines the u, v and w errors) */
   size_t max_workspace;    /* cap on the per-call device workspace in bytes; 0 = automatic
                               (a fraction of the free device memory) */
   int force_alpha;         /* >0: only consider kernels with this support (tests) */
@@ -88,7 +89,7 @@ typedef struct wg_options {
  * call's stream; filling them synchronises the stream at the end of the call. */
 typedef struct wg_stats {
   double ms_total;     /* whole call */
-  double ms_prep;      /* per-pixel correction / screen table (Eqs. R1, Rad1) */
+  double ms_prep;      /* reserved (the per-pixel correction table is built with the plan) */
   double ms_screen;    /* w-screen + zero padding into the planes (Eq. R2) */
   double ms_fft;       /* cuFFT plane transforms (separately timed stage) */
   double ms_grid;      /* (de)gridding kernels (Eqs. R3 / Rad2) */
@@ -114,12 +115,12 @@ typedef struct wg_plan_info {
   int64_t ntiles;      /* tiles in the uv grid */
   int64_t nvis;        /* visibilities in the plan (unmasked) */
   int64_t batch;       /* w-planes per batch */
-  size_t index_bytes;  /* device bytes held by the plan (visibility index) */
+  size_t index_bytes;  /* device bytes held by the plan (visibility index, per-pixel table) */
   size_t workspace_bytes; /* device bytes a degrid / grid call allocates */
   double umax, vmax, wmin, wmax; /* |u|, |v| maxima and |w| range in wavelengths */
 } wg_plan_info;
 
-/* Fill *opt with defaults (do_wstacking = 1, w_shift = 1, eps_safety = 1, rest 0). */
+/* Fill *opt with defaults (do_wstacking = 1, w_shift = 1, eps_safety = 0.8, rest 0). */
 void wg_default_options(wg_options* opt);
 
 /*
@@ -170,7 +171,7 @@ int wg_degrid(wg_plan* plan, const void* dirty, const void* wgt, void* vis, void
  * set-up and shutdown.  Such a caller creates the plan once at set-up (wg_plan_create does
  * allocate) with options.max_workspace <= WG_NOALLOC_SCRATCH_BYTES, then calls this entry
  * point as often as it likes.
- *   The per-call workspace (uv planes, cuFFT work area, per-pixel table) lives in one
+ *   The per-call workspace (uv planes and the cuFFT work area) lives in one
  * file-scope device array of WG_NOALLOC_SCRATCH_BYTES (64 MiB) that every GPU which loads the
  * library holds until the process exits.  Nothing in it has to start at zero.  This call makes
  * no cudaMalloc / cudaFree or other allocating call; the plan's cuFFT handles run on the

@@ -337,7 +337,7 @@ int choose_plan(const PlanInput& in, PlanParams& out, char* err, int errlen) {
   double nm1_min = -r2 / (1.0 + std::sqrt(1.0 - r2));
   if (in.tile != 0 && in.tile != 16 && in.tile != 32) return fail("tile must be 16 or 32");
 
-  double safety = in.eps_safety > 0 ? in.eps_safety : 1.0;
+  double safety = in.eps_safety > 0 ? in.eps_safety : kDefaultEpsSafety;
   bool found = false;
   PlanParams best;
   best.cost = std::numeric_limits<double>::infinity();

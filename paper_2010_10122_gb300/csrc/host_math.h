@@ -9,6 +9,10 @@ constexpr double kSpeedOfLight = 299792458.0;
 constexpr int kMaxAlpha = 16;
 constexpr int kMaxDeg = kMaxAlpha + 3;          // Sec. 4.2: pieces of degree alpha + 3
 constexpr int kPsiChebTerms = 28;               // psi(k) as sum_n c_n T_n(8 k^2 - 1), |k| <= 1/2
+// Kernels are chosen with table epsilon <= safety * requested epsilon.  The table epsilon is
+// the 1-D map error (App. A, Eq. maperror); the 2-D / 3-D gridding error combines the u, v and
+// w errors and was measured up to 1.17 times the table value (alpha = 4), so 0.8 by default.
+constexpr double kDefaultEpsSafety = 0.8;
 
 struct KernelRow {
   int alpha;

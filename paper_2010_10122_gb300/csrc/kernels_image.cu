@@ -26,13 +26,11 @@ __device__ __forceinline__ void sincos2pi(float c, float* s, float* co) { sincos
 __device__ __forceinline__ void sincos2pi(double c, double* s, double* co) { sincospi(2.0 * c, s, co); }
 
 // ---------------------------------------------------------------------------------------
-// prep: per pixel, corr = 1 / (n psi_u psi_v psi_w) (Eqs. R1, Rad1, with Psi the product of
-// psi over the three directions, Sec. 2) and the screen phase parameters.  With `dirty`
-// the stored value is I * corr (degrid input, Eq. R1); without, corr itself (grid output).
+// prep (once per plan): per pixel, corr = 1 / (n psi_u psi_v psi_w) (Eqs. R1, Rad1, with Psi
+// the product of psi over the three directions, Sec. 2) and the screen phase parameters.
 // ---------------------------------------------------------------------------------------
 template <typename R>
-__global__ void k_prep(const __grid_constant__ ImgParams P, const R* __restrict__ dirty,
-                       Z4<R>* __restrict__ table) {
+__global__ void k_prep(const __grid_constant__ ImgParams P, Z4<R>* __restrict__ table) {
   const Geom& g = P.g;
   int jy = blockIdx.x * blockDim.x + threadIdx.x;
   int jx = blockIdx.y;
@@ -61,9 +59,8 @@ __global__ void k_prep(const __grid_constant__ ImgParams P, const R* __restrict_
     B = g.dw * xw;
   }
   int64_t pix = (int64_t)jx * g.ny + jy;
-  double val = dirty != nullptr ? (double)dirty[pix] * corr : corr;
   Z4<R> t;
-  t.u = (R)val;
+  t.u = (R)corr;
   t.v = (R)A;
   if (sizeof(R) == 4) {
     double bhi = rint(B * 8192.0) / 8192.0;
@@ -77,9 +74,9 @@ __global__ void k_prep(const __grid_constant__ ImgParams P, const R* __restrict_
 }
 
 template <typename R>
-cudaError_t launch_prep(const ImgParams& P, const R* dirty, Z4<R>* table, cudaStream_t s) {
+cudaError_t launch_prep(const ImgParams& P, Z4<R>* table, cudaStream_t s) {
   dim3 grid((P.g.ny + 255) / 256, P.g.nx);
-  k_prep<R><<<grid, 256, 0, s>>>(P, dirty, table);
+  k_prep<R><<<grid, 256, 0, s>>>(P, table);
   return cudaGetLastError();
 }
 
@@ -90,13 +87,48 @@ __device__ __forceinline__ int cell_to_pixel(int x, int n, int N) {
   return -1;
 }
 
+// Screen values e^{2 pi i cycles(j)} for consecutive planes j = j0, j0 + 1, ...
+// FP32: each plane from its exactly reduced phase with sincospif.  FP64: sincospi at an anchor
+// plane every kAnchor planes and a complex rotation by e^{2 pi i B} in between (4 FMAs per
+// plane instead of an FP64 sincospi; the rotation's rounding grows by ~1e-16 per plane and is
+// reset at each anchor).
+constexpr int kAnchor = 16;
+template <typename R> struct ScreenIter;
+template <> struct ScreenIter<float> {
+  Z4<float> t; int j; float c, s;
+  __device__ void start(const Z4<float>& tt, int j0) { t = tt; j = j0; eval(); }
+  __device__ void eval() { float cyc = screen_cycles(t, j); sincos2pi(cyc, &s, &c); }
+  __device__ void next() { ++j; eval(); }
+};
+template <> struct ScreenIter<double> {
+  Z4<double> t; int j, k; double c, s, rc, rs;
+  __device__ void start(const Z4<double>& tt, int j0) {
+    t = tt; j = j0; k = 0;
+    double b = t.w - rint(t.w);
+    sincos2pi(b, &rs, &rc);
+    sincos2pi(screen_cycles(t, j), &s, &c);
+  }
+  __device__ void next() {
+    ++j;
+    if (++k == kAnchor) {
+      k = 0;
+      sincos2pi(screen_cycles(t, j), &s, &c);
+    } else {
+      double nc = fma(c, rc, -s * rs);
+      s = fma(s, rc, c * rs);
+      c = nc;
+    }
+  }
+};
+
 // ---------------------------------------------------------------------------------------
-// screen: planes[p] = I~ * exp(+2 pi i c_j (n - 1 - nshift)) at the image cells, 0 elsewhere
-// (Eq. R2 with the sign of Eq. rime), for global planes j = b0 .. b0 + nb - 1.
+// screen: planes[p] = I * corr * exp(+2 pi i c_j (n - 1 - nshift)) at the image cells, 0
+// elsewhere (Eqs. R1, R2 with the sign of Eq. rime), for global planes j = b0 .. b0 + nb - 1.
 // ---------------------------------------------------------------------------------------
 template <typename R>
-__global__ void k_screen(const Geom g, const Z4<R>* __restrict__ table,
-                         typename C2<R>::T* __restrict__ planes, int b0, int nb) {
+__global__ void k_screen(const Geom g, const R* __restrict__ dirty,
+                         const Z4<R>* __restrict__ table, typename C2<R>::T* __restrict__ planes,
+                         int b0, int nb) {
   using CT = typename C2<R>::T;
   int y = blockIdx.x * blockDim.x + threadIdx.x;
   int x = blockIdx.y;
@@ -109,26 +141,28 @@ __global__ void k_screen(const Geom g, const Z4<R>* __restrict__ table,
     for (int p = 0; p < nb; ++p) planes[p * ncell + cell] = zero;
     return;
   }
-  Z4<R> t = table[(int64_t)jx * g.ny + jy];
+  const int64_t pix = (int64_t)jx * g.ny + jy;
+  const Z4<R> t = table[pix];
+  const R val = dirty[pix] * t.u;   // I~ = I / (n Psi), Eq. R1
   if (!g.do_w) {
-    CT v; v.x = t.u; v.y = (R)0;
+    CT v; v.x = val; v.y = (R)0;
     planes[cell] = v;
     return;
   }
+  ScreenIter<R> it;
+  it.start(t, b0);
   for (int p = 0; p < nb; ++p) {
-    R cyc = screen_cycles(t, b0 + p);
-    R sn, cs;
-    sincos2pi(cyc, &sn, &cs);
-    CT v; v.x = t.u * cs; v.y = t.u * sn;
+    CT v; v.x = val * it.c; v.y = val * it.s;
     planes[p * ncell + cell] = v;
+    it.next();
   }
 }
 
 template <typename R>
-cudaError_t launch_screen(const Geom& g, const Z4<R>* table, typename C2<R>::T* planes, int b0,
-                          int nb, cudaStream_t s) {
+cudaError_t launch_screen(const Geom& g, const R* dirty, const Z4<R>* table,
+                          typename C2<R>::T* planes, int b0, int nb, cudaStream_t s) {
   dim3 grid((g.nv + 255) / 256, g.nu);
-  k_screen<R><<<grid, 256, 0, s>>>(g, table, planes, b0, nb);
+  k_screen<R><<<grid, 256, 0, s>>>(g, dirty, table, planes, b0, nb);
   return cudaGetLastError();
 }
 
@@ -155,12 +189,12 @@ __global__ void k_accumulate(const Geom g, const Z4<R>* __restrict__ table,
   if (!g.do_w) {
     sum = planes[cell].x;
   } else {
+    ScreenIter<R> it;
+    it.start(t, b0);
     for (int p = 0; p < nb; ++p) {
       CT h = planes[p * ncell + cell];
-      R cyc = screen_cycles(t, b0 + p);
-      R sn, cs;
-      sincos2pi(cyc, &sn, &cs);
-      sum += cs * h.x + sn * h.y;   // Re(exp(-2 pi i cyc) h)
+      sum += it.c * h.x + it.s * h.y;   // Re(exp(-2 pi i cyc) h)
+      it.next();
     }
   }
   double a = first ? (double)sum : acc[pix] + (double)sum;
@@ -179,9 +213,9 @@ cudaError_t launch_accumulate(const Geom& g, const Z4<R>* table, const typename 
 }
 
 #define WG_INST(R)                                                                          \
-  template cudaError_t launch_prep<R>(const ImgParams&, const R*, Z4<R>*, cudaStream_t);    \
-  template cudaError_t launch_screen<R>(const Geom&, const Z4<R>*, C2<R>::T*, int, int,     \
-                                        cudaStream_t);                                      \
+  template cudaError_t launch_prep<R>(const ImgParams&, Z4<R>*, cudaStream_t);              \
+  template cudaError_t launch_screen<R>(const Geom&, const R*, const Z4<R>*, C2<R>::T*, int, \
+                                        int, cudaStream_t);                                 \
   template cudaError_t launch_accumulate<R>(const Geom&, const Z4<R>*, const C2<R>::T*, int, \
                                             int, double*, bool, bool, R*, cudaStream_t);
 WG_INST(float)

@@ -113,6 +113,7 @@ struct wg_plan {
   uint32_t* meta = nullptr;
   void* z = nullptr;
   void* ph = nullptr;
+  void* table = nullptr;   // per pixel: 1 / (n Psi) and the w-screen phase parameters
   size_t index_bytes = 0;
   Coef<float> coef_f;
   Coef<double> coef_d;
@@ -134,11 +135,11 @@ void wg_default_options(wg_options* opt) {
   std::memset(opt, 0, sizeof(*opt));
   opt->do_wstacking = 1;
   opt->w_shift = 1;
-  opt->eps_safety = 1.0;
+  opt->eps_safety = kDefaultEpsSafety;
 }
 
 static int free_plan_device(wg_plan* p) {
-  void* ptrs[] = {p->chan4, p->cinv_u, p->cinv_v, p->off, p->idx, p->meta, p->z, p->ph};
+  void* ptrs[] = {p->chan4, p->cinv_u, p->cinv_v, p->off, p->idx, p->meta, p->z, p->ph, p->table};
   for (void* q : ptrs)
     if (q != nullptr) cudaFree(q);
   if (p->has_full) cufftDestroy(p->fft_full);
@@ -182,16 +183,15 @@ static int make_fft(cufftHandle* h, int prec, int64_t nu, int64_t nv, int64_t ba
 
 // per-call workspace layout
 struct Workspace {
-  size_t planes = 0, fft = 0, table = 0, acc = 0, total = 0;
+  size_t planes = 0, fft = 0, acc = 0, total = 0;
 };
 
 static Workspace workspace_layout(const wg_plan* p, int64_t batch, size_t fft_ws) {
   Workspace w;
   w.planes = align_up((size_t)batch * p->pp.nu * p->pp.nv * cplx_bytes(p->prec), 256);
   w.fft = align_up(fft_ws, 256);
-  w.table = align_up((size_t)p->g.nx * p->g.ny * 4 * (p->prec ? 8 : 4), 256);
   w.acc = align_up((size_t)p->g.nx * p->g.ny * 8, 256);
-  w.total = w.planes + w.fft + w.table + w.acc;
+  w.total = w.planes + w.fft + w.acc;
   return w;
 }
 
@@ -288,7 +288,7 @@ int wg_plan_create(const double* uvw, const double* freq, int64_t nrows, int64_t
   cudaStream_t s = (cudaStream_t)stream;
   std::unique_ptr<wg_plan> p(new wg_plan());
   if (opt) p->opt = *opt; else wg_default_options(&p->opt);
-  if (p->opt.eps_safety <= 0) p->opt.eps_safety = 1.0;
+  if (p->opt.eps_safety <= 0) p->opt.eps_safety = kDefaultEpsSafety;
   p->prec = precision;
   p->nrows = nrows; p->nchan = nchan; p->nvis_total = nrows * nchan;
   WG_CUDA(cudaGetDevice(&p->device));
@@ -368,6 +368,21 @@ int wg_plan_create(const double* uvw, const double* freq, int64_t nrows, int64_t
     if (e != cudaSuccess) return fail(set_error(WG_ERR_CUDA, "upload: %s", cudaGetErrorString(e)));
   }
   if ((rc = build_index(p.get(), uvw, mask, s)) != WG_OK) return fail(rc);
+  // per-pixel correction 1 / (n Psi) and screen phase parameters (Eqs. R1, R2, Rad1): depend
+  // only on the geometry, so they are computed once and kept with the plan
+  {
+    size_t tb = (size_t)npix_x * npix_y * 4 * (precision ? 8 : 4);
+    if ((rc = dev_alloc((unsigned char**)&p->table, tb)) != WG_OK) return fail(rc);
+    ImgParams ip;
+    ip.g = g;
+    std::memcpy(ip.psi_c, p->psi_c, sizeof(ip.psi_c));
+    ip.cinv_u = p->cinv_u; ip.cinv_v = p->cinv_v;
+    cudaError_t e = precision ? launch_prep<double>(ip, (Z4<double>*)p->table, s)
+                              : launch_prep<float>(ip, (Z4<float>*)p->table, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(set_error(WG_ERR_CUDA, "prep: %s", cudaGetErrorString(e)));
+    p->index_bytes += tb;
+  }
 
   // batch of planes: as many as the workspace budget allows
   size_t free_b = 0, total_b = 0;
@@ -502,23 +517,17 @@ static int degrid_impl(wg_plan* p, const R* dirty, const R* wgt, typename C2<R>:
   if (ws == nullptr) WG_TRY(pool_alloc((void**)&ws, w.total, p->device, s));
   auto* planes = (typename C2<R>::T*)ws;
   void* fftw = ws + w.planes;
-  auto* table = (Z4<R>*)(ws + w.planes + w.fft);
+  const auto* table = (const Z4<R>*)p->table;
   int rc = WG_OK;
-  ImgParams ip;
-  ip.g = g;
-  std::memcpy(ip.psi_c, p->psi_c, sizeof(ip.psi_c));
-  ip.cinv_u = p->cinv_u; ip.cinv_v = p->cinv_v;
   IndexView<R> ix{p->off, p->idx, p->meta, (const Z4<R>*)p->z, (const typename C2<R>::T*)p->ph};
   const Coef<R>& coef = *reinterpret_cast<const Coef<R>*>(sizeof(R) == 4 ? (const void*)&p->coef_f
                                                                          : (const void*)&p->coef_d);
   int64_t nbatches = 0;
   do {
-    cudaError_t e = launch_prep<R>(ip, dirty, table, s);
-    if (e != cudaSuccess) { rc = set_error(WG_ERR_CUDA, "prep: %s", cudaGetErrorString(e)); break; }
-    tm.mark(ST_PREP);
+    cudaError_t e = cudaSuccess;
     for (int64_t b0 = 0; b0 < g.nw; b0 += p->batch) {
       int nb = (int)std::min<int64_t>(p->batch, g.nw - b0);
-      e = launch_screen<R>(g, table, planes, (int)b0, nb, s);
+      e = launch_screen<R>(g, dirty, table, planes, (int)b0, nb, s);
       if (e != cudaSuccess) { rc = set_error(WG_ERR_CUDA, "screen: %s", cudaGetErrorString(e)); break; }
       tm.mark(ST_SCREEN);
       if ((rc = run_fft(p, nb, planes, fftw, CUFFT_FORWARD, s)) != WG_OK) break;
@@ -536,7 +545,7 @@ static int degrid_impl(wg_plan* p, const R* dirty, const R* wgt, typename C2<R>:
     std::memset(stats, 0, sizeof(*stats));
     tm.finish(stats);
     stats->n_batches = nbatches; stats->n_planes = g.nw; stats->workspace_bytes = w.total;
-    stats->n_kernels = 1 + 2 * nbatches;   // prep, then screen + degrid per batch
+    stats->n_kernels = 2 * nbatches;   // screen + degrid per batch
     stats->n_fft_calls = nbatches;
   }
   return WG_OK;
@@ -559,21 +568,15 @@ static int grid_impl(wg_plan* p, const typename C2<R>::T* vis, const R* wgt, R* 
   WG_TRY(pool_alloc((void**)&ws, w.total, p->device, s));
   auto* planes = (typename C2<R>::T*)ws;
   void* fftw = ws + w.planes;
-  auto* table = (Z4<R>*)(ws + w.planes + w.fft);
-  auto* acc = (double*)(ws + w.planes + w.fft + w.table);
+  const auto* table = (const Z4<R>*)p->table;
+  auto* acc = (double*)(ws + w.planes + w.fft);
   int rc = WG_OK;
-  ImgParams ip;
-  ip.g = g;
-  std::memcpy(ip.psi_c, p->psi_c, sizeof(ip.psi_c));
-  ip.cinv_u = p->cinv_u; ip.cinv_v = p->cinv_v;
   IndexView<R> ix{p->off, p->idx, p->meta, (const Z4<R>*)p->z, (const typename C2<R>::T*)p->ph};
   const Coef<R>& coef = *reinterpret_cast<const Coef<R>*>(sizeof(R) == 4 ? (const void*)&p->coef_f
                                                                          : (const void*)&p->coef_d);
   int64_t nbatches = 0;
   do {
-    cudaError_t e = launch_prep<R>(ip, nullptr, table, s);
-    if (e != cudaSuccess) { rc = set_error(WG_ERR_CUDA, "prep: %s", cudaGetErrorString(e)); break; }
-    tm.mark(ST_PREP);
+    cudaError_t e = cudaSuccess;
     for (int64_t b0 = 0; b0 < g.nw; b0 += p->batch) {
       int nb = (int)std::min<int64_t>(p->batch, g.nw - b0);
       e = launch_grid<R>(g, coef, ix, vis, wgt, planes, (int)b0, nb, s);
@@ -595,7 +598,7 @@ static int grid_impl(wg_plan* p, const typename C2<R>::T* vis, const R* wgt, R* 
     std::memset(stats, 0, sizeof(*stats));
     tm.finish(stats);
     stats->n_batches = nbatches; stats->n_planes = g.nw; stats->workspace_bytes = w.total;
-    stats->n_kernels = 1 + 2 * nbatches;   // prep, then grid + accumulate per batch
+    stats->n_kernels = 2 * nbatches;   // grid + accumulate per batch
     stats->n_fft_calls = nbatches;
   }
   return WG_OK;
@@ -747,7 +750,7 @@ int wg_plan_params(int64_t npix_x, int64_t npix_y, double pixsize_x, double pixs
   if (info == nullptr) return set_error(WG_ERR_ARG, "info is NULL");
   wg_options o;
   if (opt) o = *opt; else wg_default_options(&o);
-  if (o.eps_safety <= 0) o.eps_safety = 1.0;
+  if (o.eps_safety <= 0) o.eps_safety = kDefaultEpsSafety;
   PlanInput in = plan_input(npix_x, npix_y, pixsize_x, pixsize_y, epsilon, precision, o, umax,
                             vmax, wmin, wmax, nvis);
   PlanParams pp;

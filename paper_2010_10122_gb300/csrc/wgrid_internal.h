@@ -79,12 +79,12 @@ cudaError_t launch_bin_scatter(const Geom& g, const double* uvw, const double* c
                                typename C2<R>::T* ph, cudaStream_t s);
 
 // ---- image-side kernels (kernels_image.cu) -------------------------------------------
-// table: per pixel (value, A, Bhi, Blo) for f32, (value, A, B, 0) for f64.
+// table: per pixel (corr, A, Bhi, Blo) for f32, (corr, A, B, 0) for f64; corr = 1/(n Psi).
 template <typename R>
-cudaError_t launch_prep(const ImgParams& P, const R* dirty, Z4<R>* table, cudaStream_t s);
+cudaError_t launch_prep(const ImgParams& P, Z4<R>* table, cudaStream_t s);
 template <typename R>
-cudaError_t launch_screen(const Geom& g, const Z4<R>* table, typename C2<R>::T* planes,
-                          int b0, int nb, cudaStream_t s);
+cudaError_t launch_screen(const Geom& g, const R* dirty, const Z4<R>* table,
+                          typename C2<R>::T* planes, int b0, int nb, cudaStream_t s);
 template <typename R>
 cudaError_t launch_accumulate(const Geom& g, const Z4<R>* table,
                               const typename C2<R>::T* planes, int b0, int nb, double* acc,

@@ -1,0 +1,85 @@
+"""Continuous batching on the GPU: mixed degrid / grid requests of several sizes, epsilons and
+precisions over resident observations run concurrently on stream slots; every result equals
+the same request run alone, within the parity tolerances; the memory budget bounds admission."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2010_10122_gb300 import synthetic as S  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def env():
+    from paper_2010_10122_gb300 import _build
+    _build.build()
+    import paper_2010_10122_gb300 as wg  # noqa: F401
+    from paper_2010_10122_gb300.server import CudaExecutor, Request, Server, run_serial
+    assert torch.cuda.is_available()
+    obs = {
+        "o128": S.random_uvw_observation(2000, 4, 128, 128, 15.0, seed=51),
+        "o256": S.random_uvw_observation(6000, 8, 256, 256, 10.0, seed=52),
+        "o192": S.random_uvw_observation(500, 16, 192, 160, 20.0, seed=53),
+        "a512": S.array_observation(16, 40, 8, 512, 60 * S.ARCSEC, seed=54),
+    }
+    return obs, CudaExecutor, Request, Server, run_serial
+
+
+def make_requests(obs, Request, n=24, seed=0):
+    rng = np.random.default_rng(seed)
+    keys = sorted(obs)
+    reqs = []
+    t = 0.0
+    for i in range(n):
+        k = keys[rng.integers(len(keys))]
+        o = obs[k]
+        eps, prec = [(1e-4, "f32"), (1e-5, "f32"), (1e-12, "f64")][rng.integers(3)]
+        rdt = torch.float32 if prec == "f32" else torch.float64
+        cdt = torch.complex64 if prec == "f32" else torch.complex128
+        if rng.uniform() < 0.5:
+            data = torch.from_numpy(S.gaussian_image(o.npix_x, o.npix_y, seed=i)).to("cuda", rdt)
+            direction = "degrid"
+        else:
+            data = torch.from_numpy(S.complex_normal((o.nrows, o.nchan), seed=i)).to("cuda", cdt)
+            direction = "grid"
+        t += rng.exponential(0.002)
+        reqs.append(Request(k, direction, data, eps, prec, arrival=t))
+    return reqs
+
+
+def test_results_same_alone_and_in_the_mix(env):
+    obs, CudaExecutor, Request, Server, run_serial = env
+    mixed = make_requests(obs, Request)
+    ex = CudaExecutor(obs, slots=4)
+    srv = Server(ex, slots=4, memory_budget=40 << 30)
+    srv.run(mixed)
+    torch.cuda.synchronize()
+    assert all(r.error is None for r in mixed)
+    assert srv.max_inflight >= 2, "requests never overlapped"
+    alone = make_requests(obs, Request)          # same seeds -> same data
+    run_serial(CudaExecutor(obs, slots=1), alone)
+    torch.cuda.synchronize()
+    for a, b in zip(mixed, alone):
+        x, y = a.result, b.result
+        tol = 1e-6 if a.precision == "f32" else 1e-13
+        err = (x - y).abs().max().item() / max(y.abs().max().item(), 1e-30)
+        assert err <= tol, (a.obs, a.direction, a.precision, err)
+    rep = srv.report()
+    assert rep["completed"] == len(mixed) and rep["p99_s"] >= rep["p50_s"]
+
+
+def test_memory_budget_bounds_concurrency(env):
+    obs, CudaExecutor, Request, Server, run_serial = env
+    reqs = [r for r in make_requests(obs, Request, n=12, seed=3)]
+    ex = CudaExecutor(obs, slots=8)
+    for r in reqs:
+        ex.plan_bytes(r.obs, r.epsilon, r.precision)
+    resident = sum(p.info["index_bytes"] for p in ex.plans.values())
+    biggest = max(p.info["workspace_bytes"] for p in ex.plans.values())
+    budget = resident + int(1.5 * biggest)
+    srv = Server(ex, slots=8, memory_budget=budget)
+    srv.run(reqs)
+    torch.cuda.synchronize()
+    assert all(r.error is None for r in reqs)
+    assert srv.peak_memory <= budget
