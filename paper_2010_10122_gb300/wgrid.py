@@ -176,7 +176,7 @@ class Plan:
     accuracy and precision (wg_plan_create).  ``degrid`` applies R, ``grid`` R^dagger."""
 
     def __init__(self, uvw, freq, npix_x, npix_y, pixsize_x, pixsize_y, epsilon,
-                 precision="f32", mask=None, do_wstacking=True, w_shift=True, eps_safety=1.0,
+                 precision="f32", mask=None, do_wstacking=True, w_shift=True, eps_safety=None,
                  max_workspace=0, force_alpha=0, force_sigma=0.0, tile=0, grid_variant=0,
                  stream=None, device=None):
         self._h = None
@@ -191,7 +191,8 @@ class Plan:
         mask_t = _to_dev(mask, torch.uint8, dev, "mask", (self.nrows, self.nchan))
         self.npix_x, self.npix_y = int(npix_x), int(npix_y)
         opt = default_options(do_wstacking=int(bool(do_wstacking)), w_shift=int(bool(w_shift)),
-                              eps_safety=float(eps_safety), max_workspace=int(max_workspace),
+                              eps_safety=None if eps_safety is None else float(eps_safety),
+                              max_workspace=int(max_workspace),
                               force_alpha=int(force_alpha), force_sigma=float(force_sigma),
                               tile=int(tile), grid_variant=int(grid_variant))
         h = ctypes.c_void_p()

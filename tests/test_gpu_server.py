@@ -62,9 +62,12 @@ def test_results_same_alone_and_in_the_mix(env):
     torch.cuda.synchronize()
     for a, b in zip(mixed, alone):
         x, y = a.result, b.result
-        tol = 1e-6 if a.precision == "f32" else 1e-13
-        err = (x - y).abs().max().item() / max(y.abs().max().item(), 1e-30)
-        assert err <= tol, (a.obs, a.direction, a.precision, err)
+        # relative L2 difference (the parity metric): degrid and FP64 grid are deterministic
+        # (bitwise equal); FP32 grid combines footprints with shared-memory atomics, whose
+        # order varies, so two runs differ by rounding (bounded well below epsilon)
+        err = ((x - y).abs().pow(2).sum() / y.abs().pow(2).sum()).sqrt().item()
+        tol = 0.1 * a.epsilon if (a.precision == "f32" and a.direction == "grid") else 0.0
+        assert err <= tol, (a.obs, a.direction, a.precision, a.epsilon, err)
     rep = srv.report()
     assert rep["completed"] == len(mixed) and rep["p99_s"] >= rep["p50_s"]
 
