@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--oracle-seconds", type=float, default=12.0)
+    ap.add_argument("--modes", default="f32,f64",
+                    help="precision modes in a step (f32 = eps 1e-5, f64 = eps 1e-12)")
+    ap.add_argument("--grid-variant", type=int, default=0,
+                    help="gridding accumulation (0 automatic, 1 shared atomics, 2 plane-owner warps)")
     ap.add_argument("--only", default=None,
                     help="profiling aid: run only one call per step, e.g. f64:grid or f32:degrid")
     return ap.parse_args()
@@ -214,6 +218,8 @@ def main():
         dist.barrier()
     import paper_2010_10122_gb300 as wg
 
+    global MODES
+    MODES = tuple(m for m in MODES if m[0] in args.modes.split(","))
     obs, I, d = make_inputs(args.workload)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
@@ -221,7 +227,7 @@ def main():
     for prec, eps in MODES:
         rdt, cdt = (torch.float32, torch.complex64) if prec == "f32" else (torch.float64, torch.complex128)
         plans[prec] = wg.Plan(obs.uvw, obs.freq, obs.npix_x, obs.npix_y, obs.pixsize_x, obs.pixsize_y,
-                              eps, prec, device=dev)
+                              eps, prec, device=dev, grid_variant=args.grid_variant)
         dins[prec] = torch.from_numpy(I).to(dev, rdt)
         vins[prec] = torch.from_numpy(d).to(dev, cdt)
         vouts[prec] = torch.empty((obs.nrows, obs.nchan), dtype=cdt, device=dev)
@@ -271,7 +277,8 @@ def main():
     from paper_2010_10122_gb300 import replicas
     total_ms = replicas.max_over_ranks(sum(step_ms), device=dev)
     ms_per_step = total_ms / args.steps
-    value = ws * 4 * obs.nvis / (ms_per_step * 1e-3)
+    ncalls = 2 * len(MODES)
+    value = ws * ncalls * obs.nvis / (ms_per_step * 1e-3)
 
     # ---- per-call / per-stage breakdown (events inside the library, stage by stage) --------
     for _ in range(max(2, args.steps // 2)):
@@ -292,7 +299,7 @@ def main():
     for prec, eps in MODES:
         info = plans[prec].info
         m = {"eps": eps, "alpha": info["alpha"], "sigma": info["sigma"],
-             "grid": [info["nu"], info["nv"]], "nw": info["nw"], "batch": info["batch"]}
+             "uv_grid": [info["nu"], info["nv"]], "nw": info["nw"], "batch": info["batch"]}
         for direction in ("degrid", "grid"):
             sts = per_call[(prec, direction)]
             med = {k: statistics.median(s[k] for s in sts) for k in
@@ -301,9 +308,9 @@ def main():
                             **{k: round(v, 4) for k, v in med.items()}}
             launches += sts[-1]["n_kernels"]
         modes[f"{prec}_eps{eps:g}"] = m
-    f32 = modes["f32_eps1e-05"]; f64 = modes["f64_eps1e-12"]
-    t32 = f32["degrid"]["ms_total"] + f32["grid"]["ms_total"]
-    t64 = f64["degrid"]["ms_total"] + f64["grid"]["ms_total"]
+    tm = {k: m["degrid"]["ms_total"] + m["grid"]["ms_total"] for k, m in modes.items()}
+    speedup = (tm["f64_eps1e-12"] / tm["f32_eps1e-05"]
+               if "f64_eps1e-12" in tm and "f32_eps1e-05" in tm else None)
 
     # ---- roofline of the dominant library kernel ----------------------------------------------
     peaks = {}
@@ -378,7 +385,7 @@ def main():
             e1.record(stream)
             e1.synchronize()
             tot += e0.elapsed_time(e1)
-        e2e = {"value": ws * 4 * obs.nvis / (tot / args.steps * 1e-3), "unit": "vis/s",
+        e2e = {"value": ws * ncalls * obs.nvis / (tot / args.steps * 1e-3), "unit": "vis/s",
                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
 
     cpu = None
@@ -394,10 +401,11 @@ def main():
                 "config": {"workload": args.workload, "nvis": obs.nvis,
                            "npix": [obs.npix_x, obs.npix_y], "pixsize_arcsec": obs.pixsize_x / S_ARCSEC(),
                            "uv_scale": obs.uv_scale,
-                           "step": "degrid+grid at eps=1e-5 f32 and at eps=1e-12 f64, resident plans",
+                           "step": "degrid+grid at " + " and ".join(
+                               f"eps={e:g} {p}" for p, e in MODES) + ", resident plans",
                            "parallelism": f"replicas{ws}" if ws > 1 else "single",
                            "l2": "flushed between steps (256 MiB write)"},
-                "modes": modes, "fp32_vs_fp64_speedup": t64 / t32,
+                "modes": modes, "fp32_vs_fp64_speedup": speedup,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches * args.steps, "clocks": clk}
         print(json.dumps(line), flush=True)

@@ -83,6 +83,11 @@ typedef struct wg_options {
   int grid_variant;        /* gridding accumulation: 0 = automatic (shared-memory atomics for
                               WG_F32, plane-owner warps for WG_F64), 1 = shared-memory atomics,
                               2 = plane-owner warps (deterministic) */
+  int fft_impl;            /* plane FFTs: 0 = automatic (WG_F32: cuFFT C2C; WG_F64: the
+                              library's double-float FFT when epsilon >= 1e-11 and both grid
+                              sides are <= 6400, else cuFFT Z2Z), 1 = cuFFT, 2 = double-float
+                              FFT (WG_F64 only; its ~5e-15 rounding, amplified at the image
+                              edge, limits it to epsilon >= 1e-11) */
 } wg_options;
 
 /* Per-call statistics (optional output).  Stage times are CUDA-event times measured on the
@@ -243,11 +248,19 @@ int wg_plan_params(int64_t npix_x, int64_t npix_y, double pixsize_x, double pixs
                    double epsilon, int precision, const wg_options* opt, double umax,
                    double vmax, double wmin, double wmax, int64_t nvis, wg_plan_info* info);
 
-/* Planner calibration: time the batched 2-D cuFFT of `batch` n x n planes (C2C for WG_F32,
- * Z2Z for WG_F64) on the current device, `reps` executions after one warm-up, and return the
- * mean time per plane in milliseconds.  Allocates and frees its own device memory; synchronises
- * the device.  Errors: WG_ERR_ARG, WG_ERR_OOM, WG_ERR_CUFFT, WG_ERR_CUDA. */
-int wg_fft_time(int64_t n, int precision, int64_t batch, int reps, double* ms_per_plane);
+/* Planner calibration: time the batched 2-D FFT of `batch` n x n planes on the current device,
+ * `reps` executions after one warm-up, and return the mean time per plane in milliseconds.
+ * impl 1 = cuFFT (C2C for WG_F32, Z2Z for WG_F64), 2 = the library's double-float FFT
+ * (WG_F64 only).  Allocates and frees its own device memory; synchronises the device.
+ * Errors: WG_ERR_ARG (also for an unsupported size), WG_ERR_OOM, WG_ERR_CUFFT, WG_ERR_CUDA. */
+int wg_fft_time(int64_t n, int precision, int64_t batch, int reps, int impl, double* ms_per_plane);
+
+/* In-place unnormalised 2-D FFT of `batch` contiguous nu x nv complex planes (device pointer,
+ * complex64 for WG_F32, complex128 for WG_F64), sign -1 = forward (e^{-2 pi i}), +1 = inverse,
+ * with the same implementations the plans use (impl as for wg_fft_time).  Plans and frees its
+ * transform on each call (a utility, not a hot path); synchronises `stream`. */
+int wg_fft2d(void* data, int64_t nu, int64_t nv, int64_t batch, int precision, int impl, int sign,
+             void* stream);
 
 /* Library version string. */
 const char* wg_version(void);

@@ -43,7 +43,7 @@ def main():
         for prec, b in (("f32", 8), ("f64", 16)):
             batch = max(1, min(64, int((1.5 * 2**30) // (n * n * b))))
             reps = 3 if n * n * b * batch > 2**28 else 6
-            out.append(wg.fft_time(n, prec, batch=batch, reps=reps))
+            out.append(wg.fft_time(n, prec, batch=batch, reps=reps, impl=1))
         rows.append(out)
         print(f"n={n:6d} c2c {out[1]*1e3:9.2f} us/plane  z2z {out[2]*1e3:10.2f} us/plane", flush=True)
     dev = torch.cuda.get_device_name(0)

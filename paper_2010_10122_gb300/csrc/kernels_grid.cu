@@ -6,10 +6,10 @@
 //  * a group of G lanes (G = 4, 8 or 16 >= alpha) handles one visibility: lane j evaluates
 //    the j-th kernel piece in u, v and w by Horner (Sec. 4.2) and owns column j of the
 //    alpha x alpha footprint;
-//  * degrid: one CTA per tile stages tile + (alpha - 1) halo of each plane of a sub-batch in
-//    shared memory and accumulates every visibility of the tile over its planes; lanes reduce
-//    by shuffles and one lane updates the visibility (deterministic: each visibility belongs
-//    to one tile, whose CTA walks the sub-batches in order);
+//  * degrid: one CTA per (tile, sub-batch of planes) stages tile + (alpha - 1) halo of those
+//    planes in shared memory; each visibility of the tile sums its footprint over the staged
+//    planes, lanes reduce by shuffles, and the partial sum goes to a fixed slot; a finalize
+//    pass adds the slots in order (deterministic, no atomics);
 //  * grid: one CTA per (tile, sub-batch of planes) owns the T x T cells of those planes and
 //    accumulates contributions of visibilities from its own tile and the three tiles whose
 //    footprints reach into it, then writes every cell exactly once (no global atomics, no
@@ -37,12 +37,21 @@ __device__ __forceinline__ unsigned group_mask() {
 
 // ---------------------------------------------------------------------------------------
 // degrid
+//
+// CTA = (uv tile, sub-batch of bs planes).  The CTA stages tile + (alpha - 1) halo of each plane
+// of its sub-batch that some visibility of the tile needs, then every visibility of the tile
+// whose planes meet the sub-batch computes its partial sum over those planes and stores it, as
+// is, in slot (sub-batch id - first sub-batch id of the visibility) of a partial-sum array
+// indexed by the visibility's position in the index.  Sub-batches are aligned to multiples of
+// bs over the whole plane range, so a visibility meets at most `nslot` of them; a finalize pass
+// adds its slots in slot order (deterministic, no atomics) and applies the w-reference phase,
+// the Hermitian fold and the weight.
 // ---------------------------------------------------------------------------------------
 template <typename R, int G>
 __global__ void __launch_bounds__(kThreads)
 k_degrid(const Geom g, const __grid_constant__ Coef<R> coef, const IndexView<R> ix,
          const typename C2<R>::T* __restrict__ planes, int b0, int nb, int bs,
-         const R* __restrict__ wgt, typename C2<R>::T* __restrict__ vis) {
+         typename C2<R>::T* __restrict__ partial, int64_t nvis_idx) {
   using CT = typename C2<R>::T;
   extern __shared__ __align__(16) unsigned char smem[];
   R* sc = reinterpret_cast<R*>(smem);
@@ -51,92 +60,113 @@ k_degrid(const Geom g, const __grid_constant__ Coef<R> coef, const IndexView<R> 
   const int TH = T + alpha - 1;
   const int t = blockIdx.x;
   const int tu = t / g.ntv, tv = t - tu * g.ntv;
+  const int s0 = b0 + blockIdx.y * bs;
+  const int sb = min(bs, b0 + nb - s0);
+  const int sbid = s0 / bs;                       // global sub-batch id (s0 is a multiple of bs)
   const uint32_t* offt = ix.off + (int64_t)t * g.nw;
+  const uint32_t lo = offt[max(0, s0 - aw + 1)], hi = offt[min(g.nw, s0 + sb)];
+  if (lo == hi) return;                           // no visibility of this tile meets these planes
   for (int i = threadIdx.x; i < (g.deg + 1) * kMaxG; i += blockDim.x) sc[i] = coef.c[i];
+  const int64_t pstride = (int64_t)g.nu * g.nv;
+  for (int pl = 0; pl < sb; ++pl) {
+    const int p = s0 + pl;
+    if (offt[max(0, p - aw + 1)] == offt[min(p + 1, g.nw)]) continue;  // plane unused here
+    const CT* src = planes + (int64_t)(p - b0) * pstride;
+    CT* dst = st + pl * TH * TH;
+    for (int e = threadIdx.x; e < TH * TH; e += blockDim.x) {
+      int r = e / TH, c = e - r * TH;
+      int gu = tu * T + r; if (gu >= g.nu) gu -= g.nu;
+      int gv = tv * T + c; if (gv >= g.nv) gv -= g.nv;
+      dst[e] = src[(int64_t)gu * g.nv + gv];
+    }
+  }
+  __syncthreads();
+  // G lanes per visibility (lane j = piece / footprint column j).  Visibilities of a tile are
+  // sorted by first plane, so the groups of a warp have nearly the same plane range: the plane
+  // loop runs over the union of the warp's ranges (warp-uniform bounds, per-group predicate)
+  // instead of all G candidate planes.
   const int j = threadIdx.x & (G - 1);
   const int grp = threadIdx.x / G, ngrp = blockDim.x / G;
   const unsigned gmask = group_mask<G>();
-  const int64_t pstride = (int64_t)g.nu * g.nv;
-
-  for (int s0 = b0; s0 < b0 + nb; s0 += bs) {
-    const int sb = min(bs, b0 + nb - s0);
-    const uint32_t lo = offt[max(0, s0 - aw + 1)], hi = offt[min(g.nw, s0 + sb)];
-    if (lo == hi) continue;
-    __syncthreads();
-    for (int pl = 0; pl < sb; ++pl) {
-      const int p = s0 + pl;
-      if (offt[max(0, p - aw + 1)] == offt[min(p + 1, g.nw)]) continue;  // plane unused here
-      const CT* src = planes + (int64_t)(p - b0) * pstride;
-      CT* dst = st + pl * TH * TH;
-      for (int e = threadIdx.x; e < TH * TH; e += blockDim.x) {
-        int r = e / TH, c = e - r * TH;
-        int gu = tu * T + r; if (gu >= g.nu) gu -= g.nu;
-        int gv = tv * T + c; if (gv >= g.nv) gv -= g.nv;
-        dst[e] = src[(int64_t)gu * g.nv + gv];
-      }
-    }
-    __syncthreads();
-    for (uint32_t v0 = lo; v0 < hi; v0 += ngrp) {
-      const uint32_t vi = v0 + grp;
-      if (vi >= hi) continue;  // whole group
-      const uint32_t mt = ix.meta[vi];
-      const Z4<R> zz = ix.z[vi];
-      const int du = mt & 255, dv = (mt >> 8) & 255, c0 = (int)(mt >> 16);
-      const bool lj = j < alpha;
-      R pu = lj ? horner(sc, g.deg, j, zz.u) : (R)0;
-      R pv = lj ? horner(sc, g.deg, j, zz.v) : (R)0;
-      R pw = g.do_w ? (lj ? horner(sc, g.deg, j, zz.w) : (R)0) : (j == 0 ? (R)1 : (R)0);
-      R wu[G], ww[G];
+  for (uint32_t v0 = lo + (threadIdx.x >> 5) * (32 / G); v0 < hi; v0 += ngrp) {
+    const uint32_t vi = v0 + (grp % (32 / G));
+    const bool act = vi < hi;
+    uint32_t mt = 0;
+    Z4<R> zz;
+    zz.u = zz.v = zz.w = zz.pad = (R)0;
+    if (act) { mt = ix.meta[vi]; zz = ix.z[vi]; }
+    const int du = mt & 255, dv = (mt >> 8) & 255, c0 = (int)(mt >> 16);
+    const bool lj = act && j < alpha;
+    R pu = lj ? horner(sc, g.deg, j, zz.u) : (R)0;
+    R pv = lj ? horner(sc, g.deg, j, zz.v) : (R)0;
+    R pw = g.do_w ? (lj ? horner(sc, g.deg, j, zz.w) : (R)0) : (j == 0 ? (R)1 : (R)0);
+    R wu[G];
 #pragma unroll
-      for (int i = 0; i < G; ++i) {
-        wu[i] = __shfl_sync(gmask, pu, i, G);
-        ww[i] = __shfl_sync(gmask, pw, i, G);
-      }
-      R ar = (R)0, ai = (R)0;
-      if (lj) {
+    for (int i = 0; i < G; ++i) wu[i] = __shfl_sync(0xffffffffu, pu, i, G);
+    const int qlo = act ? max(0, s0 - c0) : G, qhi = act ? min(aw, s0 + sb - c0) : 0;
+    const int wlo = __reduce_min_sync(0xffffffffu, (unsigned)qlo);
+    const int whi = __reduce_max_sync(0xffffffffu, (unsigned)qhi);
+    R ar = (R)0, ai = (R)0;
+    for (int q = wlo; q < whi; ++q) {
+      const R wq = __shfl_sync(0xffffffffu, pw, q, G);
+      if (lj && q >= qlo && q < qhi) {
+        const CT* row = st + (c0 + q - s0) * TH * TH + du * TH + dv + j;
+        R sr = (R)0, si = (R)0;
 #pragma unroll
-        for (int q = 0; q < G; ++q) {
-          const int p = c0 + q;
-          if (q < aw && p >= s0 && p < s0 + sb) {
-            const CT* row = st + (p - s0) * TH * TH + du * TH + dv + j;
-            R sr = (R)0, si = (R)0;
-#pragma unroll
-            for (int i = 0; i < G; ++i) {
-              if (i < alpha) {
-                CT gv = row[i * TH];
-                sr = fma(wu[i], gv.x, sr);
-                si = fma(wu[i], gv.y, si);
-              }
-            }
-            ar = fma(ww[q], sr, ar);
-            ai = fma(ww[q], si, ai);
+        for (int i = 0; i < G; ++i) {
+          if (i < alpha) {
+            CT gv = row[i * TH];
+            sr = fma(wu[i], gv.x, sr);
+            si = fma(wu[i], gv.y, si);
           }
         }
-        ar *= pv;
-        ai *= pv;
-      }
-#pragma unroll
-      for (int o = G / 2; o > 0; o >>= 1) {
-        ar += __shfl_xor_sync(gmask, ar, o, G);
-        ai += __shfl_xor_sync(gmask, ai, o, G);
-      }
-      if (j == 0) {
-        const uint32_t id = ix.idx[vi];
-        const int64_t k = id & ~kFoldBit;
-        if (ix.ph != nullptr) {  // exp(2 pi i w nshift) times the gridded sum
-          CT ph = ix.ph[vi];
-          R r = ar * ph.x - ai * ph.y;
-          ai = ar * ph.y + ai * ph.x;
-          ar = r;
-        }
-        if (id & kFoldBit) ai = -ai;  // Hermitian fold undone: d = conj(d')
-        if (wgt != nullptr) { R w = wgt[k]; ar *= w; ai *= w; }
-        CT o = vis[k];
-        o.x += ar; o.y += ai;
-        vis[k] = o;
+        ar = fma(wq, sr, ar);
+        ai = fma(wq, si, ai);
       }
     }
+    ar *= pv;
+    ai *= pv;
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+      ar += __shfl_xor_sync(0xffffffffu, ar, o, G);
+      ai += __shfl_xor_sync(0xffffffffu, ai, o, G);
+    }
+    if (act && j == 0) {
+      const int slot = sbid - c0 / bs;
+      CT o; o.x = ar; o.y = ai;
+      partial[(int64_t)slot * nvis_idx + vi] = o;
+    }
   }
+}
+
+// vis[k] = wgt_k * fold(e^{2 pi i w_k nshift} * sum of the visibility's partial-sum slots)
+template <typename R>
+__global__ void k_degrid_finalize(const Geom g, const IndexView<R> ix,
+                                  const typename C2<R>::T* __restrict__ partial, int64_t nvis_idx,
+                                  int bs, const R* __restrict__ wgt,
+                                  typename C2<R>::T* __restrict__ vis) {
+  using CT = typename C2<R>::T;
+  const int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (pos >= nvis_idx) return;
+  const uint32_t id = ix.idx[pos];
+  const int c0 = (int)(ix.meta[pos] >> 16);
+  const int nsl = (c0 + g.alpha_w - 1) / bs - c0 / bs + 1;
+  R ar = (R)0, ai = (R)0;
+  for (int sl = 0; sl < nsl; ++sl) {
+    CT v = partial[(int64_t)sl * nvis_idx + pos];
+    ar += v.x; ai += v.y;
+  }
+  if (ix.ph != nullptr) {  // exp(2 pi i w nshift) times the gridded sum
+    CT ph = ix.ph[pos];
+    R r = ar * ph.x - ai * ph.y;
+    ai = ar * ph.y + ai * ph.x;
+    ar = r;
+  }
+  if (id & kFoldBit) ai = -ai;  // Hermitian fold undone: d = conj(d')
+  const int64_t k = id & ~kFoldBit;
+  if (wgt != nullptr) { R w = wgt[k]; ar *= w; ai *= w; }
+  CT o; o.x = ar; o.y = ai;
+  vis[k] = o;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -278,15 +308,16 @@ k_grid_owner(const Geom g, const __grid_constant__ Coef<R> coef, const IndexView
 // grid, shared-atomic variant (default for FP32)
 //
 // CTA = (uv tile, sub-batch of planes), owning the T x T cells of those planes.  A group of G
-// lanes handles one visibility (lane j = footprint column j) and adds its alpha x alpha x
-// alpha contributions with shared-memory float atomics; groups run concurrently, so cells
-// shared by overlapping footprints are combined by the atomics (summation order not fixed).
+// lanes handles one visibility (lane j = footprint column j) and adds its contributions with
+// shared-memory float atomics; groups run concurrently, so cells shared by overlapping
+// footprints are combined by the atomics (summation order not fixed).  The plane loop covers the
+// union of the warp's plane ranges (tile-sorted visibilities have nearly equal ranges).
 // ---------------------------------------------------------------------------------------
 template <typename R, int G>
 __global__ void __launch_bounds__(kThreads)
 k_grid_atomic(const Geom g, const __grid_constant__ Coef<R> coef, const IndexView<R> ix,
-       const typename C2<R>::T* __restrict__ vis, const R* __restrict__ wgt,
-       typename C2<R>::T* __restrict__ planes, int b0, int nb, int bs) {
+              const typename C2<R>::T* __restrict__ vis, const R* __restrict__ wgt,
+              typename C2<R>::T* __restrict__ planes, int b0, int nb, int bs, int pitch) {
   using CT = typename C2<R>::T;
   extern __shared__ __align__(16) unsigned char smem[];
   R* sc = reinterpret_cast<R*>(smem);
@@ -296,16 +327,18 @@ k_grid_atomic(const Geom g, const __grid_constant__ Coef<R> coef, const IndexVie
   const int tu = t / g.ntv, tv = t - tu * g.ntv;
   const int s0 = b0 + blockIdx.y * bs;
   const int sb = min(bs, b0 + nb - s0);
+  const int plane_elems = T * pitch;
   for (int i = threadIdx.x; i < (g.deg + 1) * kMaxG; i += blockDim.x) sc[i] = coef.c[i];
-  for (int e = threadIdx.x; e < sb * T * T; e += blockDim.x) {
+  for (int e = threadIdx.x; e < sb * plane_elems; e += blockDim.x) {
     CT z; z.x = (R)0; z.y = (R)0;
     acc[e] = z;
   }
   __syncthreads();
+  // G lanes per visibility (lane j = piece / footprint column j); plane loop over the union of
+  // the warp's plane ranges (warp-uniform bounds, per-group predicate)
   const int j = threadIdx.x & (G - 1);
   const int grp = threadIdx.x / G, ngrp = blockDim.x / G;
-  const unsigned gmask = group_mask<G>();
-  const bool lj = j < alpha;
+  const int gw = grp % (32 / G);
 
   // sources: this tile and the tiles one to the left / above / both, whose visibilities'
   // alpha x alpha footprints can reach into this tile (alpha - 1 <= T)
@@ -315,51 +348,58 @@ k_grid_atomic(const Geom g, const __grid_constant__ Coef<R> coef, const IndexVie
     int stv = tv + ov; if (stv < 0) stv += g.ntv;
     const uint32_t* offs = ix.off + ((int64_t)stu * g.ntv + stv) * g.nw;
     const uint32_t lo = offs[max(0, s0 - aw + 1)], hi = offs[min(g.nw, s0 + sb)];
-    for (uint32_t v0 = lo; v0 < hi; v0 += ngrp) {
-      const uint32_t vi = v0 + grp;
-      if (vi >= hi) continue;
-      const uint32_t mt = ix.meta[vi];
+    for (uint32_t v0 = lo + (threadIdx.x >> 5) * (32 / G); v0 < hi; v0 += ngrp) {
+      const uint32_t vi = v0 + gw;
+      uint32_t mt = 0;
+      if (vi < hi) mt = ix.meta[vi];
       const int ru = (int)(mt & 255) + ou * T, rv = (int)((mt >> 8) & 255) + ov * T;
-      if (ru + alpha <= 0 || rv + alpha <= 0) continue;  // footprint misses this tile
+      // footprint misses this tile (or no visibility for this group)
+      const bool act = vi < hi && ru + alpha > 0 && rv + alpha > 0;
+      if (__all_sync(0xffffffffu, !act)) continue;
       const int c0 = (int)(mt >> 16);
-      const Z4<R> zz = ix.z[vi];
-      const uint32_t id = ix.idx[vi];
-      const int64_t k = id & ~kFoldBit;
+      Z4<R> zz;
+      zz.u = zz.v = zz.w = zz.pad = (R)0;
+      R dr = (R)0, di = (R)0;
+      if (act) {
+        zz = ix.z[vi];
+        const uint32_t id = ix.idx[vi];
+        const int64_t k = id & ~kFoldBit;
+        CT d = vis[k];
+        dr = d.x; di = d.y;
+        if (wgt != nullptr) { R w = wgt[k]; dr *= w; di *= w; }
+        if (id & kFoldBit) di = -di;      // grid conj(d) at the folded coordinates
+        if (ix.ph != nullptr) {           // times conj(exp(2 pi i w nshift))
+          CT ph = ix.ph[vi];
+          R r = dr * ph.x + di * ph.y;
+          di = di * ph.x - dr * ph.y;
+          dr = r;
+        }
+      }
+      const bool lj = act && j < alpha;
       R pu = lj ? horner(sc, g.deg, j, zz.u) : (R)0;
       R pv = lj ? horner(sc, g.deg, j, zz.v) : (R)0;
       R pw = g.do_w ? (lj ? horner(sc, g.deg, j, zz.w) : (R)0) : (j == 0 ? (R)1 : (R)0);
-      R wu[G], ww[G];
+      R wu[G];
 #pragma unroll
-      for (int i = 0; i < G; ++i) {
-        wu[i] = __shfl_sync(gmask, pu, i, G);
-        ww[i] = __shfl_sync(gmask, pw, i, G);
-      }
+      for (int i = 0; i < G; ++i) wu[i] = __shfl_sync(0xffffffffu, pu, i, G);
       const int col = rv + j;
-      if (!lj || col < 0 || col >= T) continue;
-      CT d = vis[k];
-      R dr = d.x, di = d.y;
-      if (wgt != nullptr) { R w = wgt[k]; dr *= w; di *= w; }
-      if (id & kFoldBit) di = -di;      // grid conj(d) at the folded coordinates
-      if (ix.ph != nullptr) {           // times conj(exp(2 pi i w nshift))
-        CT ph = ix.ph[vi];
-        R r = dr * ph.x + di * ph.y;
-        di = di * ph.x - dr * ph.y;
-        dr = r;
-      }
+      const bool colok = lj && col >= 0 && col < T;
       dr *= pv;
       di *= pv;
-#pragma unroll
-      for (int q = 0; q < G; ++q) {
-        const int p = c0 + q;
-        if (q < aw && p >= s0 && p < s0 + sb) {
-          const R qr = dr * ww[q], qi = di * ww[q];
-          CT* base = acc + (p - s0) * T * T + col;
+      const int qlo = act ? max(0, s0 - c0) : G, qhi = act ? min(aw, s0 + sb - c0) : 0;
+      const int wlo = __reduce_min_sync(0xffffffffu, (unsigned)qlo);
+      const int whi = __reduce_max_sync(0xffffffffu, (unsigned)qhi);
+      for (int q = wlo; q < whi; ++q) {
+        const R wq = __shfl_sync(0xffffffffu, pw, q, G);
+        if (colok && q >= qlo && q < qhi) {
+          const R qr = dr * wq, qi = di * wq;
+          CT* base = acc + (c0 + q - s0) * plane_elems + col;
 #pragma unroll
           for (int i = 0; i < G; ++i) {
             const int row = ru + i;
             if (i < alpha && row >= 0 && row < T) {
-              atomicAdd(&base[row * T].x, qr * wu[i]);
-              atomicAdd(&base[row * T].y, qi * wu[i]);
+              atomicAdd(&base[row * pitch].x, qr * wu[i]);
+              atomicAdd(&base[row * pitch].y, qi * wu[i]);
             }
           }
         }
@@ -371,34 +411,43 @@ k_grid_atomic(const Geom g, const __grid_constant__ Coef<R> coef, const IndexVie
   for (int e = threadIdx.x; e < sb * T * T; e += blockDim.x) {
     const int pl = e / (T * T), rem = e - pl * T * T;
     const int r = rem / T, c = rem - r * T;
-    planes[(int64_t)(s0 - b0 + pl) * pstride + (int64_t)(tu * T + r) * g.nv + tv * T + c] = acc[e];
+    planes[(int64_t)(s0 - b0 + pl) * pstride + (int64_t)(tu * T + r) * g.nv + tv * T + c] =
+        acc[pl * plane_elems + r * pitch + c];
   }
 }
 
 // ---------------------------------------------------------------------------------------
 // launchers: sub-batch sizes from a shared-memory budget per CTA
 // ---------------------------------------------------------------------------------------
-constexpr size_t kDegridSmemBudget = 100 * 1024;
+constexpr size_t kDegridSmemBudget = 72 * 1024;
 constexpr size_t kGridSmemBudget = 110 * 1024;
 constexpr size_t kGridAtomicSmemBudget = 72 * 1024;
 
 template <typename R>
 static size_t coef_bytes() { return (kMaxDeg + 1) * kMaxG * sizeof(R); }
 
+template <typename R>
+static size_t degrid_plane_bytes(const Geom& g) {
+  const int TH = g.tile + g.alpha - 1;
+  return (size_t)TH * TH * sizeof(typename C2<R>::T);
+}
+
+template <typename R>
+int degrid_subbatch(const Geom& g) {
+  return (int)std::max<size_t>(1, (kDegridSmemBudget - coef_bytes<R>()) / degrid_plane_bytes<R>(g));
+}
+
 template <typename R, int G>
 static cudaError_t degrid_g(const Geom& g, const Coef<R>& coef, const IndexView<R>& ix,
-                            const typename C2<R>::T* planes, int b0, int nb, const R* wgt,
-                            typename C2<R>::T* vis, cudaStream_t s) {
-  const int TH = g.tile + g.alpha - 1;
-  const size_t per = (size_t)TH * TH * sizeof(typename C2<R>::T);
-  int bs = (int)std::max<size_t>(1, (kDegridSmemBudget - coef_bytes<R>()) / per);
-  bs = std::min(bs, nb);
-  size_t smem = coef_bytes<R>() + (size_t)bs * per;
+                            const typename C2<R>::T* planes, int b0, int nb, int bs,
+                            typename C2<R>::T* partial, int64_t nvis_idx, cudaStream_t s) {
+  size_t smem = coef_bytes<R>() + (size_t)std::min(bs, nb) * degrid_plane_bytes<R>(g);
   cudaError_t e = cudaFuncSetAttribute(k_degrid<R, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   int64_t ntiles = (int64_t)g.ntu * g.ntv;
-  k_degrid<R, G><<<(unsigned)ntiles, kThreads, smem, s>>>(g, coef, ix, planes, b0, nb, bs, wgt, vis);
+  dim3 grid((unsigned)ntiles, (unsigned)((nb + bs - 1) / bs));
+  k_degrid<R, G><<<grid, kThreads, smem, s>>>(g, coef, ix, planes, b0, nb, bs, partial, nvis_idx);
   return cudaGetLastError();
 }
 
@@ -428,7 +477,8 @@ template <typename R, int G>
 static cudaError_t grid_atomic_g(const Geom& g, const Coef<R>& coef, const IndexView<R>& ix,
                                  const typename C2<R>::T* vis, const R* wgt,
                                  typename C2<R>::T* planes, int b0, int nb, cudaStream_t s) {
-  const size_t per = (size_t)g.tile * g.tile * sizeof(typename C2<R>::T);
+  const int pitch = g.tile + (sizeof(R) == 4 ? 8 : 0);
+  const size_t per = (size_t)g.tile * pitch * sizeof(typename C2<R>::T);
   int bs = (int)std::max<size_t>(1, (kGridAtomicSmemBudget - coef_bytes<R>()) / per);
   bs = std::min(bs, nb);
   size_t smem = coef_bytes<R>() + (size_t)bs * per;
@@ -437,7 +487,7 @@ static cudaError_t grid_atomic_g(const Geom& g, const Coef<R>& coef, const Index
   if (e != cudaSuccess) return e;
   int64_t ntiles = (int64_t)g.ntu * g.ntv;
   dim3 grid((unsigned)ntiles, (unsigned)((nb + bs - 1) / bs));
-  k_grid_atomic<R, G><<<grid, kThreads, smem, s>>>(g, coef, ix, vis, wgt, planes, b0, nb, bs);
+  k_grid_atomic<R, G><<<grid, kThreads, smem, s>>>(g, coef, ix, vis, wgt, planes, b0, nb, bs, pitch);
   return cudaGetLastError();
 }
 
@@ -452,11 +502,21 @@ static cudaError_t grid_g(const Geom& g, const Coef<R>& coef, const IndexView<R>
 
 template <typename R>
 cudaError_t launch_degrid(const Geom& g, const Coef<R>& coef, const IndexView<R>& ix,
-                          const typename C2<R>::T* planes, int b0, int nb, const R* wgt,
-                          typename C2<R>::T* vis, cudaStream_t s) {
-  if (g.alpha <= 4) return degrid_g<R, 4>(g, coef, ix, planes, b0, nb, wgt, vis, s);
-  if (g.alpha <= 8) return degrid_g<R, 8>(g, coef, ix, planes, b0, nb, wgt, vis, s);
-  return degrid_g<R, 16>(g, coef, ix, planes, b0, nb, wgt, vis, s);
+                          const typename C2<R>::T* planes, int b0, int nb, int bs,
+                          typename C2<R>::T* partial, int64_t nvis_idx, cudaStream_t s) {
+  if (g.alpha <= 4) return degrid_g<R, 4>(g, coef, ix, planes, b0, nb, bs, partial, nvis_idx, s);
+  if (g.alpha <= 8) return degrid_g<R, 8>(g, coef, ix, planes, b0, nb, bs, partial, nvis_idx, s);
+  return degrid_g<R, 16>(g, coef, ix, planes, b0, nb, bs, partial, nvis_idx, s);
+}
+
+template <typename R>
+cudaError_t launch_degrid_finalize(const Geom& g, const IndexView<R>& ix,
+                                   const typename C2<R>::T* partial, int64_t nvis_idx, int bs,
+                                   const R* wgt, typename C2<R>::T* vis, cudaStream_t s) {
+  if (nvis_idx == 0) return cudaSuccess;
+  k_degrid_finalize<R><<<(unsigned)((nvis_idx + 255) / 256), 256, 0, s>>>(g, ix, partial, nvis_idx,
+                                                                          bs, wgt, vis);
+  return cudaGetLastError();
 }
 
 template <typename R>
@@ -469,11 +529,19 @@ cudaError_t launch_grid(const Geom& g, const Coef<R>& coef, const IndexView<R>& 
 }
 
 template cudaError_t launch_degrid<float>(const Geom&, const Coef<float>&, const IndexView<float>&,
-                                          const float2*, int, int, const float*, float2*,
+                                          const float2*, int, int, int, float2*, int64_t,
                                           cudaStream_t);
 template cudaError_t launch_degrid<double>(const Geom&, const Coef<double>&,
-                                           const IndexView<double>&, const double2*, int, int,
-                                           const double*, double2*, cudaStream_t);
+                                           const IndexView<double>&, const double2*, int, int, int,
+                                           double2*, int64_t, cudaStream_t);
+template cudaError_t launch_degrid_finalize<float>(const Geom&, const IndexView<float>&,
+                                                   const float2*, int64_t, int, const float*,
+                                                   float2*, cudaStream_t);
+template cudaError_t launch_degrid_finalize<double>(const Geom&, const IndexView<double>&,
+                                                    const double2*, int64_t, int, const double*,
+                                                    double2*, cudaStream_t);
+template int degrid_subbatch<float>(const Geom&);
+template int degrid_subbatch<double>(const Geom&);
 template cudaError_t launch_grid<float>(const Geom&, const Coef<float>&, const IndexView<float>&,
                                         const float2*, const float*, float2*, int, int,
                                         cudaStream_t);

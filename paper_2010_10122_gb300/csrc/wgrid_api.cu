@@ -122,6 +122,9 @@ struct wg_plan {
   int64_t batch = 1;
   cufftHandle fft_full = 0, fft_rem = 0;
   bool has_full = false, has_rem = false;
+  Df64Fft* dfft = nullptr;   // double-float plane FFT (WG_F64) instead of cuFFT
+  int degrid_bs = 1;         // planes per degrid CTA; batches are multiples of it
+  int nslot = 1;             // degrid partial-sum slots per visibility
   size_t fft_ws = 0;
   size_t ws_bytes = 0;
   std::mutex fft_mu;
@@ -145,6 +148,8 @@ static int free_plan_device(wg_plan* p) {
   if (p->has_full) cufftDestroy(p->fft_full);
   if (p->has_rem) cufftDestroy(p->fft_rem);
   p->has_full = p->has_rem = false;
+  df64_fft_destroy(p->dfft);
+  p->dfft = nullptr;
   return WG_OK;
 }
 
@@ -183,14 +188,16 @@ static int make_fft(cufftHandle* h, int prec, int64_t nu, int64_t nv, int64_t ba
 
 // per-call workspace layout
 struct Workspace {
-  size_t planes = 0, fft = 0, acc = 0, total = 0;
+  size_t planes = 0, fft = 0, acc = 0, total = 0;   // acc: grid accumulator / degrid partials
 };
 
 static Workspace workspace_layout(const wg_plan* p, int64_t batch, size_t fft_ws) {
   Workspace w;
   w.planes = align_up((size_t)batch * p->pp.nu * p->pp.nv * cplx_bytes(p->prec), 256);
   w.fft = align_up(fft_ws, 256);
-  w.acc = align_up((size_t)p->g.nx * p->g.ny * 8, 256);
+  size_t grid_acc = (size_t)p->g.nx * p->g.ny * 8;
+  size_t partials = (size_t)p->nslot * std::max<int64_t>(1, p->nvis) * cplx_bytes(p->prec);
+  w.acc = align_up(std::max(grid_acc, partials), 256);
   w.total = w.planes + w.fft + w.acc;
   return w;
 }
@@ -384,6 +391,15 @@ int wg_plan_create(const double* uvw, const double* freq, int64_t nrows, int64_t
     p->index_bytes += tb;
   }
 
+  // plane FFTs: the double-float FFT for FP64 planes it supports, cuFFT otherwise
+  const int fft_impl = p->opt.fft_impl;
+  if (fft_impl < 0 || fft_impl > 2) return fail(set_error(WG_ERR_ARG, "fft_impl must be 0, 1 or 2"));
+  // automatic: the double-float FFT's rounding (~5e-15 normwise) is amplified by 1 / psi at the
+  // image edge to ~1e-12 of the result, so it serves FP64 plans with epsilon >= 1e-11 only
+  bool use_df64 = precision == WG_F64 && df64_fft_supported(pp.nu, pp.nv) &&
+                  (fft_impl == 2 || (fft_impl == 0 && epsilon >= 1e-11));
+  if (fft_impl == 2 && !use_df64)
+    return fail(set_error(WG_ERR_ARG, "double-float FFT needs WG_F64 and grid sides <= 6400"));
   // batch of planes: as many as the workspace budget allows
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return fail(set_error(WG_ERR_CUDA, "cudaMemGetInfo"));
@@ -391,25 +407,43 @@ int wg_plan_create(const double* uvw, const double* freq, int64_t nrows, int64_t
   if (budget == 0) budget = std::min<size_t>(free_b / 2, (size_t)48 << 30);
   const size_t plane_b = (size_t)pp.nu * pp.nv * cplx_bytes(precision);
   int64_t B = std::max<int64_t>(1, std::min<int64_t>(pp.nw, (int64_t)(budget / (2 * plane_b))));
-  for (;;) {
-    size_t ws = 0;
-    if ((rc = make_fft(&p->fft_full, precision, pp.nu, pp.nv, B, &ws)) != WG_OK) {
-      if (rc == WG_ERR_OOM && B > 1) { B = std::max<int64_t>(1, B / 2); continue; }
-      return fail(rc);
+  p->degrid_bs = precision ? degrid_subbatch<double>(g) : degrid_subbatch<float>(g);
+  p->nslot = (g.alpha_w - 1 + p->degrid_bs - 1) / p->degrid_bs + 1;
+  // degrid sub-batches must be aligned to multiples of degrid_bs across batches
+  auto align_batch = [&](int64_t b) {
+    return b >= p->degrid_bs ? b / p->degrid_bs * p->degrid_bs : b;
+  };
+  if (B < pp.nw) B = align_batch(B);
+  if (B < p->degrid_bs && B < pp.nw) p->degrid_bs = (int)B;   // tiny budgets: one sub-batch per batch
+  p->nslot = (g.alpha_w - 1 + p->degrid_bs - 1) / p->degrid_bs + 1;
+  if (use_df64) {
+    cudaError_t e = df64_fft_create(pp.nu, pp.nv, &p->dfft);
+    if (e != cudaSuccess) return fail(set_error(WG_ERR_CUDA, "double-float FFT setup: %s", cudaGetErrorString(e)));
+    p->fft_ws = 0;
+    while (B > 1 && workspace_layout(p.get(), B, 0).total > budget)
+      B = std::max<int64_t>(1, align_batch(B * 3 / 4));
+    p->batch = B;
+  } else {
+    for (;;) {
+      size_t ws = 0;
+      if ((rc = make_fft(&p->fft_full, precision, pp.nu, pp.nv, B, &ws)) != WG_OK) {
+        if (rc == WG_ERR_OOM && B > 1) { B = std::max<int64_t>(1, align_batch(B / 2)); continue; }
+        return fail(rc);
+      }
+      p->has_full = true;
+      Workspace w = workspace_layout(p.get(), B, ws);
+      if (w.total <= budget || B == 1) { p->fft_ws = ws; break; }
+      cufftDestroy(p->fft_full); p->has_full = false;
+      B = std::max<int64_t>(1, align_batch(B * 3 / 4));
     }
-    p->has_full = true;
-    Workspace w = workspace_layout(p.get(), B, ws);
-    if (w.total <= budget || B == 1) { p->fft_ws = ws; break; }
-    cufftDestroy(p->fft_full); p->has_full = false;
-    B = std::max<int64_t>(1, B * 3 / 4);
-  }
-  p->batch = B;
-  int64_t rem = pp.nw % B;
-  if (rem != 0) {
-    size_t ws = 0;
-    if ((rc = make_fft(&p->fft_rem, precision, pp.nu, pp.nv, rem, &ws)) != WG_OK) return fail(rc);
-    p->has_rem = true;
-    p->fft_ws = std::max(p->fft_ws, ws);
+    p->batch = B;
+    int64_t rem = pp.nw % B;
+    if (rem != 0) {
+      size_t ws = 0;
+      if ((rc = make_fft(&p->fft_rem, precision, pp.nu, pp.nv, rem, &ws)) != WG_OK) return fail(rc);
+      p->has_rem = true;
+      p->fft_ws = std::max(p->fft_ws, ws);
+    }
   }
   p->ws_bytes = workspace_layout(p.get(), B, p->fft_ws).total;
   if (p->opt.max_workspace != 0 && p->ws_bytes > p->opt.max_workspace)
@@ -487,6 +521,11 @@ struct StageTimer {
 enum { ST_PREP = 0, ST_SCREEN = 1, ST_FFT = 2, ST_GRID = 3, ST_ACCUM = 4, ST_OTHER = 5 };
 
 static int run_fft(wg_plan* p, int64_t nb, void* data, void* work, int dir, cudaStream_t s) {
+  if (p->dfft != nullptr) {
+    cudaError_t e = df64_fft_exec(p->dfft, (double2*)data, nb, dir == CUFFT_FORWARD ? -1 : 1, s);
+    if (e != cudaSuccess) return set_error(WG_ERR_CUDA, "double-float FFT: %s", cudaGetErrorString(e));
+    return WG_OK;
+  }
   std::lock_guard<std::mutex> lk(p->fft_mu);
   cufftHandle h = (nb == p->batch) ? p->fft_full : p->fft_rem;
   if (nb != p->batch && !p->has_rem) return set_error(WG_ERR_INTERNAL, "no FFT plan for %lld planes", (long long)nb);
@@ -517,6 +556,7 @@ static int degrid_impl(wg_plan* p, const R* dirty, const R* wgt, typename C2<R>:
   if (ws == nullptr) WG_TRY(pool_alloc((void**)&ws, w.total, p->device, s));
   auto* planes = (typename C2<R>::T*)ws;
   void* fftw = ws + w.planes;
+  auto* partial = (typename C2<R>::T*)(ws + w.planes + w.fft);
   const auto* table = (const Z4<R>*)p->table;
   int rc = WG_OK;
   IndexView<R> ix{p->off, p->idx, p->meta, (const Z4<R>*)p->z, (const typename C2<R>::T*)p->ph};
@@ -532,11 +572,15 @@ static int degrid_impl(wg_plan* p, const R* dirty, const R* wgt, typename C2<R>:
       tm.mark(ST_SCREEN);
       if ((rc = run_fft(p, nb, planes, fftw, CUFFT_FORWARD, s)) != WG_OK) break;
       tm.mark(ST_FFT);
-      e = launch_degrid<R>(g, coef, ix, planes, (int)b0, nb, wgt, vis, s);
+      e = launch_degrid<R>(g, coef, ix, planes, (int)b0, nb, p->degrid_bs, partial, p->nvis, s);
       if (e != cudaSuccess) { rc = set_error(WG_ERR_CUDA, "degrid: %s", cudaGetErrorString(e)); break; }
       tm.mark(ST_GRID);
       ++nbatches;
     }
+    if (rc != WG_OK) break;
+    e = launch_degrid_finalize<R>(g, ix, partial, p->nvis, p->degrid_bs, wgt, vis, s);
+    if (e != cudaSuccess) { rc = set_error(WG_ERR_CUDA, "degrid finalize: %s", cudaGetErrorString(e)); break; }
+    tm.mark(ST_GRID);
   } while (0);
   if (external_ws == nullptr) pool_free(ws, s);
   p->last_stream = s;
@@ -545,7 +589,7 @@ static int degrid_impl(wg_plan* p, const R* dirty, const R* wgt, typename C2<R>:
     std::memset(stats, 0, sizeof(*stats));
     tm.finish(stats);
     stats->n_batches = nbatches; stats->n_planes = g.nw; stats->workspace_bytes = w.total;
-    stats->n_kernels = 2 * nbatches;   // screen + degrid per batch
+    stats->n_kernels = 2 * nbatches + 1;   // screen + degrid per batch, finalize
     stats->n_fft_calls = nbatches;
   }
   return WG_OK;
@@ -765,29 +809,81 @@ int wg_plan_params(int64_t npix_x, int64_t npix_y, double pixsize_x, double pixs
   return WG_OK;
 }
 
-int wg_fft_time(int64_t n, int precision, int64_t batch, int reps, double* ms_per_plane) {
+// One in-place batched 2-D transform object for the utilities below.
+struct FftUtil {
+  cufftHandle h = 0;
+  bool has_h = false;
+  Df64Fft* d = nullptr;
+  void* work = nullptr;
+  ~FftUtil() {
+    if (has_h) cufftDestroy(h);
+    df64_fft_destroy(d);
+    if (work) cudaFree(work);
+  }
+};
+
+static int fft_util_make(FftUtil& u, int64_t nu, int64_t nv, int64_t batch, int precision, int impl) {
+  if (impl == 2) {
+    if (precision != WG_F64 || !df64_fft_supported(nu, nv))
+      return set_error(WG_ERR_ARG, "double-float FFT needs WG_F64 and sides <= 6400 with factors 2,3,5,7,11");
+    cudaError_t e = df64_fft_create(nu, nv, &u.d);
+    if (e != cudaSuccess) return set_error(WG_ERR_CUDA, "double-float FFT setup: %s", cudaGetErrorString(e));
+    return WG_OK;
+  }
+  if (impl != 1) return set_error(WG_ERR_ARG, "impl must be 1 (cuFFT) or 2 (double-float)");
+  size_t ws = 0;
+  WG_TRY(make_fft(&u.h, precision, nu, nv, batch, &ws));
+  u.has_h = true;
+  if (ws > 0) WG_TRY(dev_alloc((unsigned char**)&u.work, ws));
+  WG_CUFFT(cufftSetWorkArea(u.h, u.work));
+  return WG_OK;
+}
+
+static int fft_util_exec(FftUtil& u, void* data, int64_t batch, int precision, int sign, cudaStream_t s) {
+  if (u.d != nullptr) {
+    cudaError_t e = df64_fft_exec(u.d, (double2*)data, batch, sign, s);
+    if (e != cudaSuccess) return set_error(WG_ERR_CUDA, "double-float FFT: %s", cudaGetErrorString(e));
+    return WG_OK;
+  }
+  WG_CUFFT(cufftSetStream(u.h, s));
+  int dir = sign < 0 ? CUFFT_FORWARD : CUFFT_INVERSE;
+  if (precision)
+    WG_CUFFT(cufftExecZ2Z(u.h, (cufftDoubleComplex*)data, (cufftDoubleComplex*)data, dir));
+  else
+    WG_CUFFT(cufftExecC2C(u.h, (cufftComplex*)data, (cufftComplex*)data, dir));
+  return WG_OK;
+}
+
+int wg_fft2d(void* data, int64_t nu, int64_t nv, int64_t batch, int precision, int impl, int sign,
+             void* stream) {
+  if (data == nullptr || nu < 2 || nv < 2 || batch < 1 || (precision != WG_F32 && precision != WG_F64))
+    return set_error(WG_ERR_ARG, "bad arguments");
+  FftUtil u;
+  WG_TRY(fft_util_make(u, nu, nv, batch, precision, impl));
+  cudaStream_t s = (cudaStream_t)stream;
+  WG_TRY(fft_util_exec(u, data, batch, precision, sign, s));
+  WG_CUDA(cudaStreamSynchronize(s));
+  return WG_OK;
+}
+
+int wg_fft_time(int64_t n, int precision, int64_t batch, int reps, int impl, double* ms_per_plane) {
   if (n < 2 || batch < 1 || reps < 1 || ms_per_plane == nullptr ||
       (precision != WG_F32 && precision != WG_F64))
     return set_error(WG_ERR_ARG, "bad arguments");
   size_t bytes = (size_t)n * n * batch * cplx_bytes(precision);
-  cufftHandle h;
-  size_t ws = 0;
-  WG_TRY(make_fft(&h, precision, n, n, batch, &ws));
-  void *data = nullptr, *work = nullptr;
+  FftUtil u;
+  WG_TRY(fft_util_make(u, n, n, batch, precision, impl));
+  void* data = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int rc = WG_OK;
   do {
     if ((rc = dev_alloc((unsigned char**)&data, bytes)) != WG_OK) break;
-    if (ws > 0 && (rc = dev_alloc((unsigned char**)&work, ws)) != WG_OK) break;
     if (cudaMemset(data, 0, bytes) != cudaSuccess) { rc = set_error(WG_ERR_CUDA, "memset"); break; }
-    if (cufftSetWorkArea(h, work) != CUFFT_SUCCESS) { rc = set_error(WG_ERR_CUFFT, "work area"); break; }
     cudaEventCreate(&e0); cudaEventCreate(&e1);
     float ms = 0.f;
-    for (int r = 0; r <= reps; ++r) {
+    for (int r = 0; r <= reps && rc == WG_OK; ++r) {
       if (r == 1) cudaEventRecord(e0, 0);
-      cufftResult fr = precision ? cufftExecZ2Z(h, (cufftDoubleComplex*)data, (cufftDoubleComplex*)data, CUFFT_FORWARD)
-                                 : cufftExecC2C(h, (cufftComplex*)data, (cufftComplex*)data, CUFFT_FORWARD);
-      if (fr != CUFFT_SUCCESS) { rc = set_error(WG_ERR_CUFFT, "exec %d", (int)fr); break; }
+      rc = fft_util_exec(u, data, batch, precision, -1, 0);
     }
     if (rc != WG_OK) break;
     cudaEventRecord(e1, 0);
@@ -798,8 +894,6 @@ int wg_fft_time(int64_t n, int precision, int64_t batch, int reps, double* ms_pe
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (data) cudaFree(data);
-  if (work) cudaFree(work);
-  cufftDestroy(h);
   return rc;
 }
 

@@ -64,6 +64,13 @@ struct IndexView {
 
 struct PlanImpl;
 
+// ---- double-float FFT (fft_df64.cu) -----------------------------------------------------
+struct Df64Fft;
+bool df64_fft_supported(int64_t nu, int64_t nv);
+cudaError_t df64_fft_create(int64_t nu, int64_t nv, Df64Fft** out);
+void df64_fft_destroy(Df64Fft* f);
+cudaError_t df64_fft_exec(Df64Fft* f, double2* data, int64_t batch, int sign, cudaStream_t s);
+
 // ---- index kernels (kernels_index.cu) ------------------------------------------------
 cudaError_t launch_extent(const double* uvw, int64_t nrows, unsigned long long* ext4,
                           cudaStream_t s);
@@ -91,10 +98,18 @@ cudaError_t launch_accumulate(const Geom& g, const Z4<R>* table,
                               bool first, bool last, R* dirty, cudaStream_t s);
 
 // ---- (de)gridding kernels (kernels_grid.cu) ------------------------------------------
+// planes per degrid CTA (shared-memory budget); plane batches are multiples of it
+template <typename R>
+int degrid_subbatch(const Geom& g);
+// partial sums: slot (sub-batch id - first sub-batch id of the visibility) x visibility position
 template <typename R>
 cudaError_t launch_degrid(const Geom& g, const Coef<R>& coef, const IndexView<R>& ix,
-                          const typename C2<R>::T* planes, int b0, int nb, const R* wgt,
-                          typename C2<R>::T* vis, cudaStream_t s);
+                          const typename C2<R>::T* planes, int b0, int nb, int bs,
+                          typename C2<R>::T* partial, int64_t nvis_idx, cudaStream_t s);
+template <typename R>
+cudaError_t launch_degrid_finalize(const Geom& g, const IndexView<R>& ix,
+                                   const typename C2<R>::T* partial, int64_t nvis_idx, int bs,
+                                   const R* wgt, typename C2<R>::T* vis, cudaStream_t s);
 template <typename R>
 cudaError_t launch_grid(const Geom& g, const Coef<R>& coef, const IndexView<R>& ix,
                         const typename C2<R>::T* vis, const R* wgt,

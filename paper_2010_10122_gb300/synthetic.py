@@ -117,6 +117,12 @@ def wide_1k(seed=0) -> Observation:
     return array_observation(64, 31, 8, 1024, 40 * ARCSEC, seed=seed, name="wide_1k")
 
 
+def dense_1k(seed=0) -> Observation:
+    """1024^2 at 40 arcsec with 64 antennas x 100 time steps x 8 channels (1.6e6 visibilities):
+    about the visibilities per uv cell of wide_8k on a grid small enough for profiler replays."""
+    return array_observation(64, 100, 8, 1024, 40 * ARCSEC, seed=seed, name="dense_1k")
+
+
 def wide_8k(seed=0) -> Observation:
     return array_observation(128, 193, 64, 8192, 4 * ARCSEC, seed=seed, max_rows=1_562_500,
                              name="wide_8k")
@@ -126,7 +132,8 @@ def diff_4k(seed=0) -> Observation:
     return array_observation(64, 310, 16, 4096, 4 * ARCSEC, seed=seed, name="diff_4k")
 
 
-WORKLOADS = {"tiny": tiny, "wide_1k": wide_1k, "wide_2k": wide_2k, "wide_8k": wide_8k,
+WORKLOADS = {"tiny": tiny, "wide_1k": wide_1k, "dense_1k": dense_1k, "wide_2k": wide_2k,
+             "wide_8k": wide_8k,
              "diff_4k": diff_4k}
 
 

@@ -37,7 +37,8 @@ class Options(ctypes.Structure):
     _fields_ = [("do_wstacking", ctypes.c_int), ("w_shift", ctypes.c_int),
                 ("eps_safety", ctypes.c_double), ("max_workspace", ctypes.c_size_t),
                 ("force_alpha", ctypes.c_int), ("force_sigma", ctypes.c_double),
-                ("tile", ctypes.c_int), ("grid_variant", ctypes.c_int)]
+                ("tile", ctypes.c_int), ("grid_variant", ctypes.c_int),
+                ("fft_impl", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -90,7 +91,8 @@ SIGNATURES = {
     "wg_kernel_psi": (_I, [_I, _D, _D, _VP, _VP, _I64]),
     "wg_plan_params": (_I, [_I64, _I64, _D, _D, _D, _I, ctypes.POINTER(Options), _D, _D, _D, _D,
                             _I64, ctypes.POINTER(PlanInfo)]),
-    "wg_fft_time": (_I, [_I64, _I, _I64, _I, ctypes.POINTER(_D)]),
+    "wg_fft_time": (_I, [_I64, _I, _I64, _I, _I, ctypes.POINTER(_D)]),
+    "wg_fft2d": (_I, [_VP, _I64, _I64, _I64, _I, _I, _I, _VP]),
     "wg_version": (ctypes.c_char_p, []),
 }
 
@@ -178,7 +180,7 @@ class Plan:
     def __init__(self, uvw, freq, npix_x, npix_y, pixsize_x, pixsize_y, epsilon,
                  precision="f32", mask=None, do_wstacking=True, w_shift=True, eps_safety=None,
                  max_workspace=0, force_alpha=0, force_sigma=0.0, tile=0, grid_variant=0,
-                 stream=None, device=None):
+                 fft_impl=0, stream=None, device=None):
         self._h = None
         dev = _device(device)
         self.device = dev
@@ -194,7 +196,8 @@ class Plan:
                               eps_safety=None if eps_safety is None else float(eps_safety),
                               max_workspace=int(max_workspace),
                               force_alpha=int(force_alpha), force_sigma=float(force_sigma),
-                              tile=int(tile), grid_variant=int(grid_variant))
+                              tile=int(tile), grid_variant=int(grid_variant),
+                              fft_impl=int(fft_impl))
         h = ctypes.c_void_p()
         with torch.cuda.device(dev):
             rc = lib().wg_plan_create(_ptr(uvw_t), _ptr(freq_t), self.nrows, self.nchan,
@@ -373,11 +376,25 @@ def plan_params(npix_x, npix_y, pixsize_x, pixsize_y, epsilon, precision="f32", 
     return inf.as_dict()
 
 
-def fft_time(n, precision="f32", batch=1, reps=3) -> float:
-    """Milliseconds per plane of the batched n x n cuFFT transform (planner calibration)."""
+def fft_time(n, precision="f32", batch=1, reps=3, impl=1) -> float:
+    """Milliseconds per plane of the batched n x n plane FFT (planner calibration);
+    impl 1 = cuFFT, 2 = the library's double-float FFT (f64)."""
     ms = ctypes.c_double()
-    _check(lib().wg_fft_time(int(n), _prec(precision), int(batch), int(reps), ctypes.byref(ms)))
+    _check(lib().wg_fft_time(int(n), _prec(precision), int(batch), int(reps), int(impl),
+                             ctypes.byref(ms)))
     return ms.value
+
+
+def fft2d(planes, sign=-1, impl=1, stream=None):
+    """In-place unnormalised 2-D FFT of a contiguous (batch, nu, nv) complex CUDA tensor with the
+    library's transforms (impl 1 = cuFFT, 2 = double-float, complex128 only)."""
+    if not isinstance(planes, torch.Tensor) or not planes.is_cuda or not planes.is_contiguous():
+        raise ValueError("planes must be a contiguous CUDA tensor")
+    prec = WG_F64 if planes.dtype == torch.complex128 else WG_F32
+    b, nu, nv = planes.shape if planes.ndim == 3 else (1,) + tuple(planes.shape)
+    _check(lib().wg_fft2d(_ptr(planes), int(nu), int(nv), int(b), prec, int(impl), int(sign),
+                          _stream_handle(stream, planes.device)))
+    return planes
 
 
 def version() -> str:

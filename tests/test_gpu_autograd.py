@@ -45,7 +45,9 @@ def test_gradient_fd_and_oracle_small(wg, oracle_lib, prec, eps, fd_tol):
     # central finite differences at sampled pixels
     rng = np.random.default_rng(0)
     pix = rng.choice(64 * 64, 16, replace=False)
-    h = 1e-3 * float(x.detach().double().pow(2).mean().sqrt())
+    # the loss is quadratic, so central differences are exact up to rounding for any step; a
+    # large step keeps single-precision rounding of the forward passes small against it
+    h = (1e-3 if prec == "f64" else 0.5) * float(x.detach().double().pow(2).mean().sqrt())
     fd = []
     with torch.no_grad():
         for p in pix:

@@ -21,13 +21,13 @@ from paper_2010_10122_gb300 import synthetic as S  # noqa: E402
 
 def adj_tol(prec, eps):
     """Adjointness bound (Sec. 6.1).  Rounding of the planes is amplified by 1 / psi at the image
-    edge, which grows as the planner lowers sigma for coarser epsilon: FP64 1e-14 for
-    eps <= 1e-9 (measured <= 6e-16), 5e-14 otherwise (measured up to 1.1e-14 at eps = 1e-7,
-    sigma = 1.3); FP32 1e-7 for eps <= 1e-4, 5e-7 at eps = 1e-3 (sigma = 1.15, measured 3.8e-7).
-    The paper reports < 1e-15 and < 1e-7."""
+    edge, which grows as the planner lowers sigma for coarser epsilon: FP64 with cuFFT planes
+    (eps < 1e-11) 1e-14 (measured <= 6e-16); FP64 with the double-float plane FFT
+    (eps >= 1e-11, rounding ~5e-15) 5e-13; FP32 1e-7 for eps <= 1e-4, 1e-6 at eps = 1e-3
+    (sigma = 1.15, measured up to 5.1e-7).  The paper reports < 1e-15 and < 1e-7."""
     if prec == "f64":
-        return 1e-14 if eps <= 1e-9 else 5e-14
-    return 1e-7 if eps <= 1e-4 else 5e-7
+        return 1e-14 if eps < 1e-11 else 5e-13
+    return 1e-7 if eps <= 1e-4 else 1e-6
 
 
 @pytest.fixture(scope="module")
@@ -250,3 +250,34 @@ def test_grid_variants_agree(wg, oracle_lib, small_ref, prec, eps):
         imgs.append(img)
     scale = np.abs(imgs[0]).max()
     assert np.abs(imgs[0] - imgs[1]).max() <= (1e-5 if prec == "f32" else 1e-13) * scale
+
+
+@pytest.mark.parametrize("fft_impl,eps", [(1, 1e-12), (2, 1e-11), (2, 1e-9), (1, 1e-9)])
+def test_fp64_both_fft_paths(wg, oracle_lib, small_ref, fft_impl, eps):
+    """FP64 operator with cuFFT Z2Z planes and with the double-float plane FFT (eps >= 1e-11)."""
+    I, d, rv, ri = small_ref
+    plan, vis, img = run_pair(wg, SMALL, eps, "f64", I, d, fft_impl=fft_impl)
+    assert oracle_lib.rel_l2(vis, rv) <= eps and oracle_lib.rel_l2(img, ri) <= eps
+    assert oracle_lib.adjointness_error(I, vis, d, img) < (1e-14 if fft_impl == 1 else 1e-13)
+
+
+def test_wide_8k_sampled_fp32(wg, oracle_lib):
+    """The 1e8-visibility workload (8192^2 at 4 arcsec, 128 antennas, 64 channels) at
+    eps = 1e-5 in FP32, at full size: 48 sampled visibilities and 12 sampled pixels against
+    the oracle (relative L2 over the sample)."""
+    obs = S.wide_8k()
+    I = S.point_source_image(obs.npix_x, obs.npix_y, seed=0, dtype=np.float32)
+    plan = wg.Plan(obs.uvw, obs.freq, obs.npix_x, obs.npix_y, obs.pixsize_x, obs.pixsize_y, 1e-5, "f32")
+    vis = plan.degrid(_cu(I)).cpu().numpy()
+    rng = np.random.default_rng(0)
+    vsel = rng.choice(obs.nvis, 48, replace=False)
+    rv = oracle_lib.degrid(obs.uvw, obs.freq, I.astype(np.float64), obs.pixsize_x, obs.pixsize_y,
+                           vis_index=vsel)
+    assert oracle_lib.rel_l2(vis.reshape(-1)[vsel], rv) <= 1e-5
+    del vis
+    d = S.complex_normal((obs.nrows, obs.nchan), seed=1, dtype=np.complex64)
+    img = plan.grid(_cu(d)).cpu().numpy()
+    psel = rng.choice(obs.npix_x * obs.npix_y, 12, replace=False)
+    ri = oracle_lib.grid(obs.uvw, obs.freq, d, obs.npix_x, obs.npix_y, obs.pixsize_x,
+                         obs.pixsize_y, pixel_index=psel)
+    assert oracle_lib.rel_l2(img.reshape(-1)[psel], ri) <= 1e-5

@@ -62,11 +62,12 @@ def test_results_same_alone_and_in_the_mix(env):
     torch.cuda.synchronize()
     for a, b in zip(mixed, alone):
         x, y = a.result, b.result
-        # relative L2 difference (the parity metric): degrid and FP64 grid are deterministic
-        # (bitwise equal); FP32 grid combines footprints with shared-memory atomics, whose
-        # order varies, so two runs differ by rounding (bounded well below epsilon)
+        # relative L2 difference (the parity metric).  Degrid is order-independent, so bitwise
+        # equal.  Grid sums footprints in an order that depends on the plan's bin-sort (the
+        # order inside a bucket comes from atomics) and, in FP32, on shared-memory atomics; the
+        # two runs build separate plans, so they differ by rounding, bounded well below epsilon
         err = ((x - y).abs().pow(2).sum() / y.abs().pow(2).sum()).sqrt().item()
-        tol = 0.1 * a.epsilon if (a.precision == "f32" and a.direction == "grid") else 0.0
+        tol = 0.1 * a.epsilon if a.direction == "grid" else 0.0
         assert err <= tol, (a.obs, a.direction, a.precision, a.epsilon, err)
     rep = srv.report()
     assert rep["completed"] == len(mixed) and rep["p99_s"] >= rep["p50_s"]
