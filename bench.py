@@ -50,6 +50,18 @@ def parse():
                     help="precision modes in a step (f32 = eps 1e-5, f64 = eps 1e-12)")
     ap.add_argument("--grid-variant", type=int, default=0,
                     help="gridding accumulation (0 automatic, 1 shared atomics, 2 plane-owner warps)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="precision sweep on the workload: vis/s and sampled error per epsilon")
+    ap.add_argument("--serve", action="store_true",
+                    help="continuous-batching serving benchmark (p50/p99 latency, vis/s)")
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-obs", type=int, default=16)
+    ap.add_argument("--serve-sizes", default="512,1024,2048")
+    ap.add_argument("--serve-vis", default="1e5,5e6")
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-budget-gb", type=float, default=150.0)
+    ap.add_argument("--serve-load", type=float, default=0.9,
+                    help="Poisson arrival rate as a fraction of the one-at-a-time capacity")
     ap.add_argument("--only", default=None,
                     help="profiling aid: run only one call per step, e.g. f64:grid or f32:degrid")
     return ap.parse_args()
@@ -201,10 +213,141 @@ def algorithmic_flops_per_vis(alpha):
     return 4 * alpha ** 3 + 3 * alpha * 2 * (alpha + 3)
 
 
+def run_sweep(args):
+    """Precision sweep (eps in {1e-3, 1e-5 FP32; 1e-7, 1e-10, 1e-12 FP64}): per epsilon the
+    degrid and grid vis/s (CUDA events, resident plan) and the relative L2 error against the
+    oracle on sampled visibilities / pixels.  One JSON line per epsilon."""
+    import torch
+    import paper_2010_10122_gb300 as wg
+    from oracle import direct
+    direct.build()
+    obs, I, d = make_inputs(args.workload)
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(0)
+    vsel = rng.choice(obs.nvis, 256, replace=False)
+    psel = rng.choice(obs.npix_x * obs.npix_y, 8, replace=False)
+    rv = direct.degrid(obs.uvw, obs.freq, I, obs.pixsize_x, obs.pixsize_y, vis_index=vsel)
+    ri = direct.grid(obs.uvw, obs.freq, d, obs.npix_x, obs.npix_y, obs.pixsize_x, obs.pixsize_y,
+                     pixel_index=psel)
+    for prec, eps in (("f32", 1e-3), ("f32", 1e-5), ("f64", 1e-7), ("f64", 1e-10), ("f64", 1e-12)):
+        rdt, cdt = (torch.float32, torch.complex64) if prec == "f32" else (torch.float64, torch.complex128)
+        plan = wg.Plan(obs.uvw, obs.freq, obs.npix_x, obs.npix_y, obs.pixsize_x, obs.pixsize_y,
+                       eps, prec, device=dev)
+        dimg = torch.from_numpy(I).to(dev, rdt)
+        dvis = torch.from_numpy(d).to(dev, cdt)
+        res = {}
+        for direction in ("degrid", "grid"):
+            fn = (lambda: plan.degrid(dimg)) if direction == "degrid" else (lambda: plan.grid(dvis))
+            out = fn()
+            torch.cuda.synchronize()
+            times = []
+            for _ in range(max(1, args.steps)):
+                e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(); out = fn(); e1.record(); e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+            ms = statistics.median(times)
+            o = out.cpu().numpy()
+            err = (direct.rel_l2(o.reshape(-1)[vsel], rv) if direction == "degrid"
+                   else direct.rel_l2(o.reshape(-1)[psel], ri))
+            res[direction] = {"ms": ms, "vis_per_s": obs.nvis / (ms * 1e-3), "rel_l2_err": err}
+            del out
+        info = plan.info
+        print(json.dumps({"sweep": args.workload, "precision": prec, "eps": eps,
+                          "alpha": info["alpha"], "sigma": info["sigma"],
+                          "uv_grid": [info["nu"], info["nv"]], "nw": info["nw"],
+                          "fft": "double-float" if (prec == "f64" and eps >= 1e-11 and
+                                                    max(info["nu"], info["nv"]) <= 6400) else "cuFFT",
+                          **res, "error_sample": "256 visibilities / 8 pixels vs the FP64 oracle"}),
+              flush=True)
+        plan.close()
+        del dimg, dvis
+        torch.cuda.empty_cache()
+    return 0
+
+
+def run_serve(args):
+    """Continuous-batching serving benchmark: resident observations of mixed image sizes and
+    visibility counts, Poisson arrivals of mixed degrid / grid requests at mixed epsilons,
+    admission by stream slots and a device-memory budget.  Reports p50 / p99 latency and
+    aggregate vis/s, next to one-at-a-time execution of the same requests."""
+    import torch
+    from paper_2010_10122_gb300 import synthetic as S
+    from paper_2010_10122_gb300.server import CudaExecutor, Request, Server, run_serial
+    rng = np.random.default_rng(5)
+    sizes = [int(x) for x in args.serve_sizes.split(",")]
+    vlo, vhi = (float(x) for x in args.serve_vis.split(","))
+    obs = {}
+    for i in range(args.serve_obs):
+        n = sizes[rng.integers(len(sizes))]
+        nvis = int(np.exp(rng.uniform(np.log(vlo), np.log(vhi))))
+        nt = max(1, nvis // (2016 * 16))
+        pix = 20 * S.ARCSEC * 2048 / n      # same field of view (11.4 deg) for every size
+        obs[f"obs{i}"] = S.array_observation(64, nt, 16, n, pix, seed=100 + i)
+    keys = sorted(obs)
+    epss = [(1e-4, "f32"), (1e-5, "f32"), (1e-12, "f64")]
+
+    def make(nreq, seed):
+        r = np.random.default_rng(seed)
+        out = []
+        for _ in range(nreq):
+            k = keys[r.integers(len(keys))]
+            o = obs[k]
+            eps, prec = epss[r.integers(len(epss))]
+            if r.uniform() < 0.5:
+                data = torch.from_numpy(S.point_source_image(o.npix_x, o.npix_y, seed=int(r.integers(1 << 30)))).to(
+                    "cuda", torch.float32 if prec == "f32" else torch.float64)
+                out.append(Request(k, "degrid", data, eps, prec))
+            else:
+                data = torch.from_numpy(S.complex_normal((o.nrows, o.nchan), seed=int(r.integers(1 << 30)))).to(
+                    "cuda", torch.complex64 if prec == "f32" else torch.complex128)
+                out.append(Request(k, "grid", data, eps, prec))
+        return out
+
+    budget = int(args.serve_budget_gb * (1 << 30))
+    ex = CudaExecutor(obs, slots=args.serve_slots, workspace_cap=8 << 30)
+    # resident plans for every (observation, epsilon) a request can use
+    for k in keys:
+        for eps, prec in epss:
+            ex.plan_bytes(k, eps, prec)
+    # one-at-a-time capacity on a calibration set, then the same request mix served
+    calib = make(max(8, args.serve_requests // 10), 1)
+    run_serial(ex, calib)                       # warm-up
+    torch.cuda.synchronize()
+    reqs_serial = make(args.serve_requests, 2)
+    t_serial = run_serial(ex, reqs_serial)
+    rate = args.serve_load * len(reqs_serial) / t_serial
+    reqs = make(args.serve_requests, 2)
+    t = 0.0
+    for r in reqs:
+        t += rng.exponential(1.0 / rate)
+        r.arrival = t
+    srv = Server(ex, slots=args.serve_slots, memory_budget=budget)
+    srv.run(reqs)
+    torch.cuda.synchronize()
+    rep = srv.report()
+    nvis_total = sum(r.nvis for r in reqs if r.error is None)
+    line = {"serve": "continuous batching", "requests": len(reqs), "observations": len(obs),
+            "image_sizes": sizes, "vis_range": [vlo, vhi], "eps_mix": [e for e, _ in epss],
+            "slots": args.serve_slots, "budget_gb": args.serve_budget_gb,
+            "arrival_rate_per_s": rate, "load": args.serve_load,
+            "p50_latency_s": rep.get("p50_s"), "p99_latency_s": rep.get("p99_s"),
+            "mean_latency_s": rep.get("mean_s"), "vis_per_s": rep.get("vis_per_s"),
+            "failed": rep.get("failed"), "max_inflight": rep.get("max_inflight"),
+            "peak_memory_gb": rep.get("peak_memory", 0) / (1 << 30),
+            "one_at_a_time_s": t_serial, "one_at_a_time_vis_per_s": nvis_total / t_serial,
+            "served_span_s": rep.get("span_s")}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep:
+        return run_sweep(args)
+    if args.serve:
+        return run_serve(args)
     import torch
     import torch.distributed as dist
     ws, rank, local = dist_env()

@@ -85,9 +85,11 @@ typedef struct wg_options {
                               2 = plane-owner warps (deterministic) */
   int fft_impl;            /* plane FFTs: 0 = automatic (WG_F32: cuFFT C2C; WG_F64: the
                               library's double-float FFT when epsilon >= 1e-11 and both grid
-                              sides are <= 6400, else cuFFT Z2Z), 1 = cuFFT, 2 = double-float
-                              FFT (WG_F64 only; its ~5e-15 rounding, amplified at the image
-                              edge, limits it to epsilon >= 1e-11) */
+                              sides are <= 6400, else pruned cuFFT Z2Z), 1 = cuFFT 2-D,
+                              2 = double-float FFT (WG_F64 only; its ~5e-15 rounding, amplified
+                              at the image edge, limits it to epsilon >= 1e-11), 3 = pruned
+                              cuFFT (WG_F64 only: 1-D passes that skip the plane rows outside
+                              the image) */
 } wg_options;
 
 /* Per-call statistics (optional output).  Stage times are CUDA-event times measured on the

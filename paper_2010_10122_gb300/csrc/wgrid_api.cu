@@ -123,6 +123,11 @@ struct wg_plan {
   cufftHandle fft_full = 0, fft_rem = 0;
   bool has_full = false, has_rem = false;
   Df64Fft* dfft = nullptr;   // double-float plane FFT (WG_F64) instead of cuFFT
+  // pruned cuFFT transform: 1-D row plan (rows of one image block) and column plan (all
+  // columns of one plane); rows outside the image are skipped
+  bool pruned = false;
+  cufftHandle fft_row = 0, fft_col = 0;
+  bool has_row = false, has_col = false;
   int degrid_bs = 1;         // planes per degrid CTA; batches are multiples of it
   int nslot = 1;             // degrid partial-sum slots per visibility
   size_t fft_ws = 0;
@@ -150,6 +155,9 @@ static int free_plan_device(wg_plan* p) {
   p->has_full = p->has_rem = false;
   df64_fft_destroy(p->dfft);
   p->dfft = nullptr;
+  if (p->has_row) cufftDestroy(p->fft_row);
+  if (p->has_col) cufftDestroy(p->fft_col);
+  p->has_row = p->has_col = false;
   return WG_OK;
 }
 
@@ -182,6 +190,27 @@ static int make_fft(cufftHandle* h, int prec, int64_t nu, int64_t nv, int64_t ba
     if (r == CUFFT_ALLOC_FAILED) return set_error(WG_ERR_OOM, "cuFFT plan allocation failed");
     return set_error(WG_ERR_CUFFT, "cufftMakePlanMany64 (%lld x %lld x %lld): %d", n[0], n[1],
                      (long long)batch, (int)r);
+  }
+  return WG_OK;
+}
+
+// 1-D batched transform of length n: element stride `stride`, transforms `dist` apart
+static int make_fft1d(cufftHandle* h, int prec, int64_t n, int64_t stride, int64_t dist,
+                      int64_t batch, size_t* ws) {
+  WG_CUFFT(cufftCreate(h));
+  cufftResult r = cufftSetAutoAllocation(*h, 0);
+  if (r != CUFFT_SUCCESS) {
+    cufftDestroy(*h);
+    return set_error(WG_ERR_CUFFT, "cufftSetAutoAllocation: %d", (int)r);
+  }
+  long long nn[1] = {(long long)n}, emb[1] = {(long long)n};
+  r = cufftMakePlanMany64(*h, 1, nn, emb, (long long)stride, (long long)dist, emb,
+                          (long long)stride, (long long)dist, prec ? CUFFT_Z2Z : CUFFT_C2C,
+                          (long long)batch, ws);
+  if (r != CUFFT_SUCCESS) {
+    cufftDestroy(*h);
+    if (r == CUFFT_ALLOC_FAILED) return set_error(WG_ERR_OOM, "cuFFT plan allocation failed");
+    return set_error(WG_ERR_CUFFT, "cufftMakePlanMany64 1-D (%lld): %d", nn[0], (int)r);
   }
   return WG_OK;
 }
@@ -393,7 +422,7 @@ int wg_plan_create(const double* uvw, const double* freq, int64_t nrows, int64_t
 
   // plane FFTs: the double-float FFT for FP64 planes it supports, cuFFT otherwise
   const int fft_impl = p->opt.fft_impl;
-  if (fft_impl < 0 || fft_impl > 2) return fail(set_error(WG_ERR_ARG, "fft_impl must be 0, 1 or 2"));
+  if (fft_impl < 0 || fft_impl > 3) return fail(set_error(WG_ERR_ARG, "fft_impl must be 0, 1, 2 or 3"));
   // automatic: the double-float FFT's rounding (~5e-15 normwise) is amplified by 1 / psi at the
   // image edge to ~1e-12 of the result, so it serves FP64 plans with epsilon >= 1e-11 only
   bool use_df64 = precision == WG_F64 && df64_fft_supported(pp.nu, pp.nv) &&
@@ -421,6 +450,19 @@ int wg_plan_create(const double* uvw, const double* freq, int64_t nrows, int64_t
     if (e != cudaSuccess) return fail(set_error(WG_ERR_CUDA, "double-float FFT setup: %s", cudaGetErrorString(e)));
     p->fft_ws = 0;
     while (B > 1 && workspace_layout(p.get(), B, 0).total > budget)
+      B = std::max<int64_t>(1, align_batch(B * 3 / 4));
+    p->batch = B;
+  } else if (precision == WG_F64 && (fft_impl == 3 || fft_impl == 0)) {
+    // FP64 cuFFT is compute-bound on GB300: transform only the rows that hold the image
+    // (degrid: rows are the first pass; grid: the last pass, on the rows the image needs)
+    p->pruned = true;
+    size_t ws_r = 0, ws_c = 0;
+    if ((rc = make_fft1d(&p->fft_row, precision, pp.nv, 1, pp.nv, npix_x / 2, &ws_r)) != WG_OK) return fail(rc);
+    p->has_row = true;
+    if ((rc = make_fft1d(&p->fft_col, precision, pp.nu, pp.nv, 1, pp.nv, &ws_c)) != WG_OK) return fail(rc);
+    p->has_col = true;
+    p->fft_ws = std::max(ws_r, ws_c);
+    while (B > 1 && workspace_layout(p.get(), B, p->fft_ws).total > budget)
       B = std::max<int64_t>(1, align_batch(B * 3 / 4));
     p->batch = B;
   } else {
@@ -527,6 +569,31 @@ static int run_fft(wg_plan* p, int64_t nb, void* data, void* work, int dir, cuda
     return WG_OK;
   }
   std::lock_guard<std::mutex> lk(p->fft_mu);
+  if (p->pruned) {
+    const int64_t nu = p->pp.nu, nv = p->pp.nv, half = p->g.nx / 2;
+    const int64_t plane = nu * nv;
+    auto* base = (cufftDoubleComplex*)data;
+    WG_CUFFT(cufftSetStream(p->fft_row, s));
+    WG_CUFFT(cufftSetWorkArea(p->fft_row, work));
+    WG_CUFFT(cufftSetStream(p->fft_col, s));
+    WG_CUFFT(cufftSetWorkArea(p->fft_col, work));
+    auto rows = [&](cufftDoubleComplex* pl) -> int {
+      WG_CUFFT(cufftExecZ2Z(p->fft_row, pl, pl, dir));                              // rows [0, nx/2)
+      WG_CUFFT(cufftExecZ2Z(p->fft_row, pl + (nu - half) * nv, pl + (nu - half) * nv, dir));  // last nx/2
+      return WG_OK;
+    };
+    for (int64_t b = 0; b < nb; ++b) {
+      cufftDoubleComplex* pl = base + b * plane;
+      if (dir == CUFFT_FORWARD) {   // degrid: image rows hold the only nonzero data
+        WG_TRY(rows(pl));
+        WG_CUFFT(cufftExecZ2Z(p->fft_col, pl, pl, dir));
+      } else {                      // grid: the image reads only its own rows
+        WG_CUFFT(cufftExecZ2Z(p->fft_col, pl, pl, dir));
+        WG_TRY(rows(pl));
+      }
+    }
+    return WG_OK;
+  }
   cufftHandle h = (nb == p->batch) ? p->fft_full : p->fft_rem;
   if (nb != p->batch && !p->has_rem) return set_error(WG_ERR_INTERNAL, "no FFT plan for %lld planes", (long long)nb);
   WG_CUFFT(cufftSetStream(h, s));
