@@ -29,6 +29,15 @@ __device__ __forceinline__ R horner(const R* __restrict__ sc, int deg, int j, R 
   return r;
 }
 
+// piece j of direction d (0 u, 1 v, 2 w) of indexed visibility vi: from the per-call table when
+// present, else by Horner from the shared-memory coefficients
+template <typename R>
+__device__ __forceinline__ R kernel_value(const IndexView<R>& ix, const R* __restrict__ sc,
+                                          int deg, uint32_t vi, int d, int j, R z) {
+  if (ix.wts != nullptr) return ix.wts[(int64_t)vi * (3 * kMaxG) + d * kMaxG + j];
+  return horner(sc, deg, j, z);
+}
+
 template <int G>
 __device__ __forceinline__ unsigned group_mask() {
   const int lane = threadIdx.x & 31;
@@ -97,9 +106,9 @@ k_degrid(const Geom g, const __grid_constant__ Coef<R> coef, const IndexView<R> 
     if (act) { mt = ix.meta[vi]; zz = ix.z[vi]; }
     const int du = mt & 255, dv = (mt >> 8) & 255, c0 = (int)(mt >> 16);
     const bool lj = act && j < alpha;
-    R pu = lj ? horner(sc, g.deg, j, zz.u) : (R)0;
-    R pv = lj ? horner(sc, g.deg, j, zz.v) : (R)0;
-    R pw = g.do_w ? (lj ? horner(sc, g.deg, j, zz.w) : (R)0) : (j == 0 ? (R)1 : (R)0);
+    R pu = lj ? kernel_value(ix, sc, g.deg, vi, 0, j, zz.u) : (R)0;
+    R pv = lj ? kernel_value(ix, sc, g.deg, vi, 1, j, zz.v) : (R)0;
+    R pw = g.do_w ? (lj ? kernel_value(ix, sc, g.deg, vi, 2, j, zz.w) : (R)0) : (j == 0 ? (R)1 : (R)0);
     R wu[G];
 #pragma unroll
     for (int i = 0; i < G; ++i) wu[i] = __shfl_sync(0xffffffffu, pu, i, G);
@@ -241,9 +250,10 @@ k_grid_owner(const Geom g, const __grid_constant__ Coef<R> coef, const IndexView
         if (!hit) continue;
         const Z4<R> zz = ix.z[vi];
         const bool lj = j1 < alpha;
-        stg->wu[v][j1] = lj ? horner(sc, g.deg, j1, zz.u) : (R)0;
-        stg->wv[v][j1] = lj ? horner(sc, g.deg, j1, zz.v) : (R)0;
-        stg->ww[v][j1] = g.do_w ? (lj ? horner(sc, g.deg, j1, zz.w) : (R)0) : (j1 == 0 ? (R)1 : (R)0);
+        stg->wu[v][j1] = lj ? kernel_value(ix, sc, g.deg, vi, 0, j1, zz.u) : (R)0;
+        stg->wv[v][j1] = lj ? kernel_value(ix, sc, g.deg, vi, 1, j1, zz.v) : (R)0;
+        stg->ww[v][j1] = g.do_w ? (lj ? kernel_value(ix, sc, g.deg, vi, 2, j1, zz.w) : (R)0)
+                                : (j1 == 0 ? (R)1 : (R)0);
         if (j1 == 0) {
           const uint32_t id = ix.idx[vi];
           const int64_t k = id & ~kFoldBit;
@@ -376,9 +386,9 @@ k_grid_atomic(const Geom g, const __grid_constant__ Coef<R> coef, const IndexVie
         }
       }
       const bool lj = act && j < alpha;
-      R pu = lj ? horner(sc, g.deg, j, zz.u) : (R)0;
-      R pv = lj ? horner(sc, g.deg, j, zz.v) : (R)0;
-      R pw = g.do_w ? (lj ? horner(sc, g.deg, j, zz.w) : (R)0) : (j == 0 ? (R)1 : (R)0);
+      R pu = lj ? kernel_value(ix, sc, g.deg, vi, 0, j, zz.u) : (R)0;
+      R pv = lj ? kernel_value(ix, sc, g.deg, vi, 1, j, zz.v) : (R)0;
+      R pw = g.do_w ? (lj ? kernel_value(ix, sc, g.deg, vi, 2, j, zz.w) : (R)0) : (j == 0 ? (R)1 : (R)0);
       R wu[G];
 #pragma unroll
       for (int i = 0; i < G; ++i) wu[i] = __shfl_sync(0xffffffffu, pu, i, G);
@@ -415,6 +425,39 @@ k_grid_atomic(const Geom g, const __grid_constant__ Coef<R> coef, const IndexVie
         acc[pl * plane_elems + r * pitch + c];
   }
 }
+
+// ---------------------------------------------------------------------------------------
+// per-call kernel values: one thread per (visibility, direction, piece), Horner (Sec. 4.2)
+// ---------------------------------------------------------------------------------------
+template <typename R>
+__global__ void k_weights(const Geom g, const __grid_constant__ Coef<R> coef, const IndexView<R> ix,
+                          int64_t nvis_idx, R* __restrict__ wts) {
+  __shared__ R sc[(kMaxDeg + 1) * kMaxG];
+  for (int i = threadIdx.x; i < (g.deg + 1) * kMaxG; i += blockDim.x) sc[i] = coef.c[i];
+  __syncthreads();
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nvis_idx * 3 * kMaxG) return;
+  const int64_t pos = e / (3 * kMaxG);
+  const int r = (int)(e - pos * 3 * kMaxG), d = r / kMaxG, j = r - d * kMaxG;
+  const Z4<R> zz = ix.z[pos];
+  R v = (R)0;
+  if (j < g.alpha) v = horner(sc, g.deg, j, d == 0 ? zz.u : (d == 1 ? zz.v : zz.w));
+  wts[e] = v;
+}
+
+template <typename R>
+cudaError_t launch_weights(const Geom& g, const Coef<R>& coef, const IndexView<R>& ix,
+                           int64_t nvis_idx, R* wts, cudaStream_t s) {
+  if (nvis_idx == 0) return cudaSuccess;
+  const int64_t n = nvis_idx * 3 * kMaxG;
+  k_weights<R><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, coef, ix, nvis_idx, wts);
+  return cudaGetLastError();
+}
+template cudaError_t launch_weights<float>(const Geom&, const Coef<float>&, const IndexView<float>&,
+                                           int64_t, float*, cudaStream_t);
+template cudaError_t launch_weights<double>(const Geom&, const Coef<double>&,
+                                            const IndexView<double>&, int64_t, double*,
+                                            cudaStream_t);
 
 // ---------------------------------------------------------------------------------------
 // launchers: sub-batch sizes from a shared-memory budget per CTA

@@ -129,6 +129,7 @@ struct wg_plan {
   cufftHandle fft_row = 0, fft_col = 0;
   bool has_row = false, has_col = false;
   int degrid_bs = 1;         // planes per degrid CTA; batches are multiples of it
+  bool use_wts = false;      // per-call kernel-value table (FP64, when it fits the workspace)
   int nslot = 1;             // degrid partial-sum slots per visibility
   size_t fft_ws = 0;
   size_t ws_bytes = 0;
@@ -217,7 +218,7 @@ static int make_fft1d(cufftHandle* h, int prec, int64_t n, int64_t stride, int64
 
 // per-call workspace layout
 struct Workspace {
-  size_t planes = 0, fft = 0, acc = 0, total = 0;   // acc: grid accumulator / degrid partials
+  size_t planes = 0, fft = 0, acc = 0, wts = 0, total = 0;   // acc: grid accumulator / degrid partials
 };
 
 static Workspace workspace_layout(const wg_plan* p, int64_t batch, size_t fft_ws) {
@@ -227,7 +228,8 @@ static Workspace workspace_layout(const wg_plan* p, int64_t batch, size_t fft_ws
   size_t grid_acc = (size_t)p->g.nx * p->g.ny * 8;
   size_t partials = (size_t)p->nslot * std::max<int64_t>(1, p->nvis) * cplx_bytes(p->prec);
   w.acc = align_up(std::max(grid_acc, partials), 256);
-  w.total = w.planes + w.fft + w.acc;
+  w.wts = p->use_wts ? align_up((size_t)std::max<int64_t>(1, p->nvis) * 3 * kMaxG * 8, 256) : 0;
+  w.total = w.planes + w.fft + w.acc + w.wts;
   return w;
 }
 
@@ -444,6 +446,10 @@ int wg_plan_create(const double* uvw, const double* freq, int64_t nrows, int64_t
   };
   if (B < pp.nw) B = align_batch(B);
   if (B < p->degrid_bs && B < pp.nw) p->degrid_bs = (int)B;   // tiny budgets: one sub-batch per batch
+  // FP64: evaluate each visibility's kernel values once per call (the FP64 pipe is the limit
+  // of the (de)gridding kernels, and Horner on every tile / sub-batch visit doubles its work)
+  p->use_wts = precision == WG_F64 &&
+               (size_t)p->nvis * 3 * kMaxG * 8 <= budget / 4;
   p->nslot = (g.alpha_w - 1 + p->degrid_bs - 1) / p->degrid_bs + 1;
   if (use_df64) {
     cudaError_t e = df64_fft_create(pp.nu, pp.nv, &p->dfft);
@@ -624,14 +630,19 @@ static int degrid_impl(wg_plan* p, const R* dirty, const R* wgt, typename C2<R>:
   auto* planes = (typename C2<R>::T*)ws;
   void* fftw = ws + w.planes;
   auto* partial = (typename C2<R>::T*)(ws + w.planes + w.fft);
+  R* wts = w.wts ? (R*)(ws + w.planes + w.fft + w.acc) : nullptr;
   const auto* table = (const Z4<R>*)p->table;
   int rc = WG_OK;
-  IndexView<R> ix{p->off, p->idx, p->meta, (const Z4<R>*)p->z, (const typename C2<R>::T*)p->ph};
+  IndexView<R> ix{p->off, p->idx, p->meta, (const Z4<R>*)p->z, (const typename C2<R>::T*)p->ph, wts};
   const Coef<R>& coef = *reinterpret_cast<const Coef<R>*>(sizeof(R) == 4 ? (const void*)&p->coef_f
                                                                          : (const void*)&p->coef_d);
   int64_t nbatches = 0;
   do {
     cudaError_t e = cudaSuccess;
+    if (wts != nullptr) {
+      e = launch_weights<R>(g, coef, ix, p->nvis, wts, s);
+      if (e != cudaSuccess) { rc = set_error(WG_ERR_CUDA, "weights: %s", cudaGetErrorString(e)); break; }
+    }
     for (int64_t b0 = 0; b0 < g.nw; b0 += p->batch) {
       int nb = (int)std::min<int64_t>(p->batch, g.nw - b0);
       e = launch_screen<R>(g, dirty, table, planes, (int)b0, nb, s);
@@ -656,7 +667,7 @@ static int degrid_impl(wg_plan* p, const R* dirty, const R* wgt, typename C2<R>:
     std::memset(stats, 0, sizeof(*stats));
     tm.finish(stats);
     stats->n_batches = nbatches; stats->n_planes = g.nw; stats->workspace_bytes = w.total;
-    stats->n_kernels = 2 * nbatches + 1;   // screen + degrid per batch, finalize
+    stats->n_kernels = 2 * nbatches + 1 + (wts != nullptr);   // screen + degrid per batch, finalize, weights
     stats->n_fft_calls = nbatches;
   }
   return WG_OK;
@@ -681,13 +692,18 @@ static int grid_impl(wg_plan* p, const typename C2<R>::T* vis, const R* wgt, R* 
   void* fftw = ws + w.planes;
   const auto* table = (const Z4<R>*)p->table;
   auto* acc = (double*)(ws + w.planes + w.fft);
+  R* wts = w.wts ? (R*)(ws + w.planes + w.fft + w.acc) : nullptr;
   int rc = WG_OK;
-  IndexView<R> ix{p->off, p->idx, p->meta, (const Z4<R>*)p->z, (const typename C2<R>::T*)p->ph};
+  IndexView<R> ix{p->off, p->idx, p->meta, (const Z4<R>*)p->z, (const typename C2<R>::T*)p->ph, wts};
   const Coef<R>& coef = *reinterpret_cast<const Coef<R>*>(sizeof(R) == 4 ? (const void*)&p->coef_f
                                                                          : (const void*)&p->coef_d);
   int64_t nbatches = 0;
   do {
     cudaError_t e = cudaSuccess;
+    if (wts != nullptr) {
+      e = launch_weights<R>(g, coef, ix, p->nvis, wts, s);
+      if (e != cudaSuccess) { rc = set_error(WG_ERR_CUDA, "weights: %s", cudaGetErrorString(e)); break; }
+    }
     for (int64_t b0 = 0; b0 < g.nw; b0 += p->batch) {
       int nb = (int)std::min<int64_t>(p->batch, g.nw - b0);
       e = launch_grid<R>(g, coef, ix, vis, wgt, planes, (int)b0, nb, s);
@@ -709,7 +725,7 @@ static int grid_impl(wg_plan* p, const typename C2<R>::T* vis, const R* wgt, R* 
     std::memset(stats, 0, sizeof(*stats));
     tm.finish(stats);
     stats->n_batches = nbatches; stats->n_planes = g.nw; stats->workspace_bytes = w.total;
-    stats->n_kernels = 2 * nbatches;   // grid + accumulate per batch
+    stats->n_kernels = 2 * nbatches + (wts != nullptr);   // grid + accumulate per batch, weights
     stats->n_fft_calls = nbatches;
   }
   return WG_OK;

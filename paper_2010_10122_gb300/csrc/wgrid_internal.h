@@ -60,6 +60,9 @@ struct IndexView {
   const uint32_t* meta;
   const Z4<R>* z;
   const typename C2<R>::T* ph;  // may be null
+  // optional per-visibility kernel values (u, v, w pieces, each padded to kMaxG), evaluated once
+  // per call instead of on every (tile, sub-batch) visit; null = evaluate by Horner
+  const R* wts;
 };
 
 struct PlanImpl;
@@ -98,6 +101,10 @@ cudaError_t launch_accumulate(const Geom& g, const Z4<R>* table,
                               bool first, bool last, R* dirty, cudaStream_t s);
 
 // ---- (de)gridding kernels (kernels_grid.cu) ------------------------------------------
+// kernel values of every indexed visibility: wts[pos * 3 kMaxG + d kMaxG + j]
+template <typename R>
+cudaError_t launch_weights(const Geom& g, const Coef<R>& coef, const IndexView<R>& ix,
+                           int64_t nvis_idx, R* wts, cudaStream_t s);
 // planes per degrid CTA (shared-memory budget); plane batches are multiples of it
 template <typename R>
 int degrid_subbatch(const Geom& g);
