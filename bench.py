@@ -34,6 +34,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "visibilities/sec for degrid and grid on 1 GB300 at eps=1e-5 (FP32) and 1e-12 (FP64)"
 MODES = (("f32", 1e-5), ("f64", 1e-12))
+FFT_NAMES = {1: "cuFFT 2-D", 2: "double-float (pruned rows)", 3: "cuFFT Z2Z (pruned rows)"}
 
 
 def parse():
@@ -255,8 +256,7 @@ def run_sweep(args):
         print(json.dumps({"sweep": args.workload, "precision": prec, "eps": eps,
                           "alpha": info["alpha"], "sigma": info["sigma"],
                           "uv_grid": [info["nu"], info["nv"]], "nw": info["nw"],
-                          "fft": "double-float" if (prec == "f64" and eps >= 1e-11 and
-                                                    max(info["nu"], info["nv"]) <= 6400) else "cuFFT",
+                          "fft": FFT_NAMES[info["fft_impl"]], "err_model": info["err_model"],
                           **res, "error_sample": "256 visibilities / 8 pixels vs the FP64 oracle"}),
               flush=True)
         plan.close()
@@ -442,7 +442,8 @@ def main():
     for prec, eps in MODES:
         info = plans[prec].info
         m = {"eps": eps, "alpha": info["alpha"], "sigma": info["sigma"],
-             "uv_grid": [info["nu"], info["nv"]], "nw": info["nw"], "batch": info["batch"]}
+             "uv_grid": [info["nu"], info["nv"]], "nw": info["nw"], "batch": info["batch"],
+             "fft": FFT_NAMES[info["fft_impl"]], "err_model": info["err_model"]}
         for direction in ("degrid", "grid"):
             sts = per_call[(prec, direction)]
             med = {k: statistics.median(s[k] for s in sts) for k in

@@ -84,12 +84,12 @@ typedef struct wg_options {
                               WG_F32, plane-owner warps for WG_F64), 1 = shared-memory atomics,
                               2 = plane-owner warps (deterministic) */
   int fft_impl;            /* plane FFTs: 0 = automatic (WG_F32: cuFFT C2C; WG_F64: the
-                              library's double-float FFT when epsilon >= 1e-11 and both grid
-                              sides are <= 6400, else pruned cuFFT Z2Z), 1 = cuFFT 2-D,
-                              2 = double-float FFT (WG_F64 only; its ~5e-15 rounding, amplified
-                              at the image edge, limits it to epsilon >= 1e-11), 3 = pruned
-                              cuFFT (WG_F64 only: 1-D passes that skip the plane rows outside
-                              the image) */
+                              cheaper of 2 and 3 whose predicted error fits epsilon),
+                              1 = cuFFT 2-D, 2 = the library's double-float FFT (WG_F64 only,
+                              grid sides <= 6400; its ~5e-15 rounding is amplified by the
+                              1 / psi correction, so the planner may raise sigma for it),
+                              3 = pruned cuFFT Z2Z (WG_F64 only: 1-D passes that skip the
+                              plane rows outside the image) */
 } wg_options;
 
 /* Per-call statistics (optional output).  Stage times are CUDA-event times measured on the
@@ -125,6 +125,13 @@ typedef struct wg_plan_info {
   size_t index_bytes;  /* device bytes held by the plan (visibility index, per-pixel table) */
   size_t workspace_bytes; /* device bytes a degrid / grid call allocates */
   double umax, vmax, wmin, wmax; /* |u|, |v| maxima and |w| range in wavelengths */
+  int fft_impl;        /* plane FFT used: 1 cuFFT 2-D, 2 double-float, 3 pruned cuFFT Z2Z */
+  double rounding_gain; /* factor by which relative plane rounding reaches the result: rms of
+                           1 / (n psi_u psi_v psi_w) over the image x (int phi^2)^(3/2) */
+  double err_model;    /* predicted eps_rms: kernel term eps_kernel / eps_safety and plane
+                          rounding term (unit roundoff x 0.06 log2(nu nv) x rounding_gain),
+                          added in quadrature; the planner keeps it <= epsilon unless sigma
+                          is forced */
 } wg_plan_info;
 
 /* Fill *opt with defaults (do_wstacking = 1, w_shift = 1, eps_safety = 0.8, rest 0). */

@@ -2,8 +2,9 @@
 to csrc/fft_table.inc (run on the target GPU; the library must be built).
 
 Candidates: n = 32 m for 4 <= m <= 512 with m 11-smooth (FFT-friendly multiples of the uv
-tile).  For each n the batched 2-D C2C (FP32) and Z2Z (FP64) transforms are timed through the
-library's wg_fft_time entry point with ~1-2 GiB of planes per batch.  The planner uses the
+tile).  For each n the batched 2-D C2C (FP32) and Z2Z (FP64) cuFFT transforms and the library's
+double-float FFT (FP64 planes, sides up to 6400) are timed through the library's wg_fft_time
+entry point with ~1-2 GiB of planes per batch.  The planner uses the
 table to pick, for each oversampling factor, the fastest size >= sigma * n and to price the
 FFT stage in its cost model (Sec. 4.1).
 
@@ -40,18 +41,23 @@ def main():
             continue
         n = 32 * m
         out = [n]
-        for prec, b in (("f32", 8), ("f64", 16)):
+        for prec, b, impl in (("f32", 8, 1), ("f64", 16, 1), ("f64", 16, 2)):
+            if impl == 2 and n > 6400:
+                out.append(0.0)
+                continue
             batch = max(1, min(64, int((1.5 * 2**30) // (n * n * b))))
             reps = 3 if n * n * b * batch > 2**28 else 6
-            out.append(wg.fft_time(n, prec, batch=batch, reps=reps, impl=1))
+            out.append(wg.fft_time(n, prec, batch=batch, reps=reps, impl=impl))
         rows.append(out)
-        print(f"n={n:6d} c2c {out[1]*1e3:9.2f} us/plane  z2z {out[2]*1e3:10.2f} us/plane", flush=True)
+        print(f"n={n:6d} c2c {out[1]*1e3:9.2f} us/plane  z2z {out[2]*1e3:10.2f} us/plane  "
+              f"df64 {out[3]*1e3:10.2f} us/plane", flush=True)
     dev = torch.cuda.get_device_name(0)
     with open(args.out, "w") as f:
         f.write(f"// cuFFT batched 2-D plane transform times on {dev}, measured by\n")
-        f.write("// paper_2010_10122_gb300/calibrate_fft.py: {n, ms per plane C2C, ms per plane Z2Z}\n")
-        for n, a, b in rows:
-            f.write(f"{{{n}, {a:.6g}, {b:.6g}}},\n")
+        f.write("// paper_2010_10122_gb300/calibrate_fft.py: {n, ms per plane C2C, ms per plane Z2Z, "
+                "ms per plane double-float}\n")
+        for n, a, b, c in rows:
+            f.write(f"{{{n}, {a:.6g}, {b:.6g}, {c:.6g}}},\n")
     print(f"wrote {len(rows)} sizes to {args.out} in {time.time() - t0:.0f} s")
 
 

@@ -4,19 +4,22 @@
 // transforms the dominant cost of the FP64 (eps ~ 1e-12) mode.  Here every value is carried as
 // an unevaluated sum hi + lo of two floats (48-bit significand); additions use the two-sum and
 // products the fma-based two-product error-free transformations, so a radix-8 butterfly costs a
-// few hundred FP32 operations instead of FP64 ones.  Normwise accuracy of a length-3200
-// transform is ~5e-15 relative (vs ~3e-16 for FP64), well below what eps >= 1e-12 needs.
+// few hundred FP32 operations instead of FP64 ones.  Normwise accuracy of a 3200 x 3200
+// transform is ~5e-15 relative (vs ~2e-16 for FP64); the planner accounts for it (its
+// rounding is amplified by the 1 / psi correction, see plane_rounding / rounding_gain).
 //
-// Algorithm: each 1-D transform is a mixed-radix (8, 4, 2, 5, 3 and a generic radix for 7 / 11)
-// Stockham autosort FFT run by one CTA in shared memory with ping-pong buffers; the 2-D plane
-// transform is a pass over rows (contiguous) followed by a pass over columns (several adjacent
-// columns per CTA, so the strided global accesses move whole sectors).  Planes stay complex128
-// in global memory: the row pass splits doubles into df64 on load and stores df64, the column
-// pass loads df64 and joins back to doubles on store.  Transforms are unnormalised, forward =
-// e^{-2 pi i}, like cuFFT's.
+// Algorithm: each 1-D transform is a mixed-radix (8 and 4 for the power of two, 5, 3, a
+// generic radix for 7 / 11, 2 only for n = 2 * odd) Stockham autosort FFT run by one CTA per
+// line with about n / 8 threads (one radix-8 butterfly each) over two n-element shared-memory
+// buffers (ping-pong); up to n = 3584 two CTAs share an SM.  The 2-D plane transform is a pass
+// over rows (contiguous) and a pass over columns.  Planes stay complex128 in global memory:
+// the first pass splits doubles into df64 on load and stores df64, the second loads df64 and
+// joins back to doubles on store.  Transforms are unnormalised, forward = e^{-2 pi i}, like
+// cuFFT's.
 #include <cmath>
 #include <cstring>
 
+#include "host_math.h"
 #include "wgrid_internal.h"
 
 namespace wg {
@@ -99,6 +102,7 @@ constexpr int kMaxStages = 24;
 struct FftLine {
   int n;                     // transform length
   int nst;                   // number of radix stages
+  int threads;               // CTA size of the line kernel (about n / 8)
   int radix[kMaxStages];
   const float4* tw;          // e^{-2 pi i t / n}, t = 0 .. n - 1, df64
   DftConst k;
@@ -187,109 +191,103 @@ __device__ __forceinline__ void dft_generic(cdd* x, bool fwd, const float4* __re
   for (int q = 0; q < R; ++q) x[q] = y[q];
 }
 
-// One radix-R Stockham stage over `lines` lines of length n held in shared memory.
+template <int R>
+__device__ __forceinline__ void butterfly(cdd* x, bool fwd, const FftLine& L) {
+  if (R == 2) dft2(x);
+  else if (R == 3) dft3(x, fwd, L.k);
+  else if (R == 4) dft4(x, fwd);
+  else if (R == 5) dft5(x, fwd, L.k);
+  else if (R == 8) dft8(x, fwd, L.k);
+  else dft_generic<R>(x, fwd, L.tw, L.n);
+}
+
+// One radix-R Stockham stage of a length-n line: butterfly j (j = tid, tid + T, ...) reads
+// src[j + kk M], twiddles, transforms and writes dst[(j / Ns) Ns R + j mod Ns + q Ns].
 template <int R>
 __device__ __forceinline__ void stage(const float4* __restrict__ src, float4* __restrict__ dst,
-                                      int n, int lines, int Ns, bool fwd, const FftLine& L) {
+                                      int n, int Ns, bool fwd, const FftLine& L) {
   const int M = n / R;
   const int tstep = n / (Ns * R);
-  for (int b = threadIdx.x; b < lines * M; b += blockDim.x) {
-    const int line = b / M, j = b - line * M;
-    const float4* s = src + line * n;
-    float4* d = dst + line * n;
-    const int jm = j % Ns;
+  for (int j = threadIdx.x; j < M; j += blockDim.x) {
+    const int jq = j / Ns, jm = j - jq * Ns;
     cdd x[R];
 #pragma unroll
-    for (int kk = 0; kk < R; ++kk) x[kk] = load_cdd(s[j + kk * M]);
+    for (int kk = 0; kk < R; ++kk) x[kk] = load_cdd(src[j + kk * M]);
     if (Ns > 1) {
+      // jm * kk * tstep < Ns * R * tstep = n: no reduction needed
 #pragma unroll
-      for (int kk = 1; kk < R; ++kk) x[kk] = c_mul(x[kk], twiddle(L.tw, (jm * kk * tstep) % n, fwd));
+      for (int kk = 1; kk < R; ++kk) x[kk] = c_mul(x[kk], twiddle(L.tw, jm * kk * tstep, fwd));
     }
-    if (R == 2) dft2(x);
-    else if (R == 4) dft4(x, fwd);
-    else if (R == 8) dft8(x, fwd, L.k);
-    else if (R == 3) dft3(x, fwd, L.k);
-    else if (R == 5) dft5(x, fwd, L.k);
-    else dft_generic<R>(x, fwd, L.tw, n);
-    const int idx = (j / Ns) * Ns * R + jm;
+    butterfly<R>(x, fwd, L);
+    const int idx = jq * Ns * R + jm;
 #pragma unroll
-    for (int q = 0; q < R; ++q) d[idx + q * Ns] = store_cdd(x[q]);
+    for (int q = 0; q < R; ++q) dst[idx + q * Ns] = store_cdd(x[q]);
   }
 }
 
-// Transform `lines` lines of one plane: line c, element i at global offset
-// base + (line0 + c) * line_stride + i * elem_stride (complex elements).
-// mode 0: load doubles, store df64; mode 1: load df64, store doubles.
-__global__ void __launch_bounds__(256)
+// Transform one line per CTA: line `line` of plane `plane`, element i at global offset
+// plane * plane_elems + line * line_stride + i * elem_stride (complex elements).  The plane's
+// transformed lines are numbered 0 .. lines_per_plane - 1; those from `split` on are shifted
+// by `skip` (a pass over the first and last rows of a plane only, skipping the middle).
+// mode 0: load doubles, store df64; mode 1: load df64, store doubles.  Two n-element
+// shared-memory buffers (ping-pong); kAll adds the rare radices 2, 7 and 11, kept out of the
+// common instance so that its register allocation is not burdened with them.
+template <int TMAX, int MINB, bool kAll>
+__global__ void __launch_bounds__(TMAX, MINB)
 k_fft_lines(const __grid_constant__ FftLine L, void* __restrict__ data, int64_t plane_elems,
-            int lines_per_plane, int lines, int64_t line_stride, int64_t elem_stride, int mode,
-            int fwd) {
+            int lines_per_plane, int64_t line_stride, int64_t elem_stride, int mode, int fwd,
+            int split, int skip) {
   extern __shared__ __align__(16) float4 fsm[];
   const int n = L.n;
-  float4* bufA = fsm;
-  float4* bufB = fsm + (size_t)lines * n;
-  const int blocks_per_plane = lines_per_plane / lines;
-  const int plane = blockIdx.x / blocks_per_plane;
-  const int line0 = (blockIdx.x - plane * blocks_per_plane) * lines;
-  const int64_t base = (int64_t)plane * plane_elems + (int64_t)line0 * line_stride;
-  const int total = lines * n;
-  // load: consecutive threads walk the contiguous direction (coalesced global access)
+  const int T = blockDim.x;
+  float4* src = fsm;
+  float4* dst = fsm + n;
+  const int plane = blockIdx.x / lines_per_plane;
+  int line = blockIdx.x - plane * lines_per_plane;
+  if (line >= split) line += skip;
+  const int64_t base = (int64_t)plane * plane_elems + (int64_t)line * line_stride;
   if (mode == 0) {
-    const double2* in = reinterpret_cast<const double2*>(data);
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-      int c, i;
-      if (elem_stride == 1) { c = e / n; i = e - c * n; }
-      else { i = e / lines; c = e - i * lines; }
-      double2 v = in[base + c * line_stride + i * elem_stride];
+    const double2* in = reinterpret_cast<const double2*>(data) + base;
+    for (int i = threadIdx.x; i < n; i += T) {
+      double2 v = in[i * elem_stride];
       cdd x; x.r = split_double(v.x); x.i = split_double(v.y);
-      bufA[c * n + i] = store_cdd(x);
+      src[i] = store_cdd(x);
     }
   } else {
-    const float4* in = reinterpret_cast<const float4*>(data);
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-      int c, i;
-      if (elem_stride == 1) { c = e / n; i = e - c * n; }
-      else { i = e / lines; c = e - i * lines; }
-      bufA[c * n + i] = in[base + c * line_stride + i * elem_stride];
-    }
+    const float4* in = reinterpret_cast<const float4*>(data) + base;
+    for (int i = threadIdx.x; i < n; i += T) src[i] = in[i * elem_stride];
   }
   __syncthreads();
-  float4* src = bufA;
-  float4* dst = bufB;
   int Ns = 1;
   const bool f = fwd != 0;
   for (int s = 0; s < L.nst; ++s) {
     const int R = L.radix[s];
     switch (R) {
-      case 2: stage<2>(src, dst, n, lines, Ns, f, L); break;
-      case 3: stage<3>(src, dst, n, lines, Ns, f, L); break;
-      case 4: stage<4>(src, dst, n, lines, Ns, f, L); break;
-      case 5: stage<5>(src, dst, n, lines, Ns, f, L); break;
-      case 7: stage<7>(src, dst, n, lines, Ns, f, L); break;
-      case 8: stage<8>(src, dst, n, lines, Ns, f, L); break;
-      default: stage<11>(src, dst, n, lines, Ns, f, L); break;
+      case 3: stage<3>(src, dst, n, Ns, f, L); break;
+      case 4: stage<4>(src, dst, n, Ns, f, L); break;
+      case 5: stage<5>(src, dst, n, Ns, f, L); break;
+      case 8: stage<8>(src, dst, n, Ns, f, L); break;
+      default:
+        if (kAll) {
+          if (R == 2) stage<2>(src, dst, n, Ns, f, L);
+          else if (R == 7) stage<7>(src, dst, n, Ns, f, L);
+          else stage<11>(src, dst, n, Ns, f, L);
+        }
+        break;
     }
-    Ns *= R;
     __syncthreads();
     float4* t = src; src = dst; dst = t;
+    Ns *= R;
   }
   if (mode == 0) {
-    float4* out = reinterpret_cast<float4*>(data);
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-      int c, i;
-      if (elem_stride == 1) { c = e / n; i = e - c * n; }
-      else { i = e / lines; c = e - i * lines; }
-      out[base + c * line_stride + i * elem_stride] = src[c * n + i];
-    }
+    float4* out = reinterpret_cast<float4*>(data) + base;
+    for (int i = threadIdx.x; i < n; i += T) out[i * elem_stride] = src[i];
   } else {
-    double2* out = reinterpret_cast<double2*>(data);
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
-      int c, i;
-      if (elem_stride == 1) { c = e / n; i = e - c * n; }
-      else { i = e / lines; c = e - i * lines; }
-      cdd x = load_cdd(src[c * n + i]);
+    double2* out = reinterpret_cast<double2*>(data) + base;
+    for (int i = threadIdx.x; i < n; i += T) {
+      cdd x = load_cdd(src[i]);
       double2 v; v.x = join_double(x.r); v.y = join_double(x.i);
-      out[base + c * line_stride + i * elem_stride] = v;
+      out[i * elem_stride] = v;
     }
   }
 }
@@ -297,16 +295,6 @@ k_fft_lines(const __grid_constant__ FftLine L, void* __restrict__ data, int64_t 
 // ---------------------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------------------
-static bool factor_radices(int n, int* r, int* nst) {
-  int k = 0;
-  int m = n;
-  for (int p : {8, 4, 2, 5, 3, 7, 11}) {
-    while (m % p == 0 && k < kMaxStages) { r[k++] = p; m /= p; }
-  }
-  *nst = k;
-  return m == 1;
-}
-
 static dd host_dd(long double v) {
   float h = (float)v;
   float l = (float)(v - (long double)h);
@@ -319,22 +307,21 @@ struct Df64Fft {
   FftLine lu, lv;
   float4* tw_u = nullptr;
   float4* tw_v = nullptr;
-  int lines_u = 1, lines_v = 1;   // lines per CTA in the column / row pass
 };
 
-static constexpr size_t kFftSmem = 200 * 1024;
+// Two lines of n df64 complex values in shared memory per CTA (two CTAs per SM up to n = 3584).
+static constexpr int64_t kMaxSide = kDf64MaxSide;
 
-bool df64_fft_supported(int64_t nu, int64_t nv) {
-  int r[kMaxStages], k;
-  if (nu > (int64_t)(kFftSmem / (2 * sizeof(float4))) || nv > (int64_t)(kFftSmem / (2 * sizeof(float4))))
-    return false;
-  return factor_radices((int)nu, r, &k) && factor_radices((int)nv, r, &k);
-}
+bool df64_fft_supported(int64_t nu, int64_t nv) { return df64_side_ok(nu) && df64_side_ok(nv); }
 
 static cudaError_t make_line(int n, FftLine* L, float4** tw) {
   std::memset(L, 0, sizeof(*L));
   L->n = n;
-  if (!factor_radices(n, L->radix, &L->nst)) return cudaErrorInvalidValue;
+  Df64LinePlan lp;
+  if (!df64_line_plan(n, &lp) || lp.nst > kMaxStages) return cudaErrorInvalidValue;
+  L->nst = lp.nst;
+  L->threads = lp.threads;
+  for (int i = 0; i < lp.nst; ++i) L->radix[i] = lp.radix[i];
   std::vector<float4> h(n);
   const long double two_pi = 6.283185307179586476925286766559L;
   for (int t = 0; t < n; ++t) {
@@ -357,27 +344,24 @@ static cudaError_t make_line(int n, FftLine* L, float4** tw) {
   return cudaSuccess;
 }
 
-static int lines_per_cta(int n, int lines_total) {
-  int c = (int)(kFftSmem / (2 * sizeof(float4) * (size_t)n));
-  c = std::max(1, std::min(c, 8));
-  while (c > 1 && lines_total % c != 0) --c;
-  return c;
-}
-
 cudaError_t df64_fft_create(int64_t nu, int64_t nv, Df64Fft** out) {
   *out = nullptr;
+  if (!df64_fft_supported(nu, nv)) return cudaErrorInvalidValue;
   Df64Fft* f = new Df64Fft();
   f->nu = (int)nu; f->nv = (int)nv;
   cudaError_t e = make_line((int)nu, &f->lu, &f->tw_u);
   if (e == cudaSuccess) e = make_line((int)nv, &f->lv, &f->tw_v);
+  const int smax = (int)(2 * kMaxSide * sizeof(float4));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft_lines<448, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft_lines<448, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft_lines<832, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft_lines<832, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
   if (e != cudaSuccess) {
     if (f->tw_u) cudaFree(f->tw_u);
     if (f->tw_v) cudaFree(f->tw_v);
     delete f;
     return e;
   }
-  f->lines_v = lines_per_cta(f->nv, f->nu);   // row pass: rows of length nv
-  f->lines_u = lines_per_cta(f->nu, f->nv);   // column pass: columns of length nu
   *out = f;
   return cudaSuccess;
 }
@@ -389,30 +373,55 @@ void df64_fft_destroy(Df64Fft* f) {
   delete f;
 }
 
+static cudaError_t launch_lines(const FftLine& L, double2* data, int64_t batch, int64_t plane,
+                                int lines_per_plane, int64_t line_stride, int64_t elem_stride,
+                                int mode, int fwd, int split, int skip, cudaStream_t s) {
+  if (lines_per_plane == 0 || batch == 0) return cudaSuccess;
+  const size_t smem = 2 * sizeof(float4) * (size_t)L.n;
+  const int64_t blocks = batch * lines_per_plane;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  bool common = true;   // radices 8, 4, 5, 3 only
+  for (int i = 0; i < L.nst; ++i)
+    if (L.radix[i] == 2 || L.radix[i] == 7 || L.radix[i] == 11) common = false;
+#define WG_LINES(TM, MB, A)                                                                     \
+  k_fft_lines<TM, MB, A><<<(unsigned)blocks, L.threads, smem, s>>>(                             \
+      L, data, plane, lines_per_plane, line_stride, elem_stride, mode, fwd, split, skip)
+  if (L.threads <= 448) {
+    if (common) WG_LINES(448, 2, false); else WG_LINES(448, 2, true);
+  } else {
+    if (common) WG_LINES(832, 1, false); else WG_LINES(832, 1, true);
+  }
+#undef WG_LINES
+  return cudaGetLastError();
+}
+
 // In-place transform of `batch` nu x nv complex128 planes; sign -1 forward, +1 inverse.
-cudaError_t df64_fft_exec(Df64Fft* f, double2* data, int64_t batch, int sign, cudaStream_t s) {
+// keep_rows = 0: the full 2-D transform.  keep_rows = k (even, < nu): only the first and last
+// k/2 rows of a plane matter -- forward: they hold the only nonzero input, so the row pass
+// runs over them alone (the other rows stay zero, whose bits are the same in both formats);
+// inverse: only they are read afterwards, so the column pass runs first and the row pass over
+// them alone, and the other rows are left in the intermediate (df64) format.
+cudaError_t df64_fft_exec(Df64Fft* f, double2* data, int64_t batch, int sign, cudaStream_t s,
+                          int64_t keep_rows) {
   const int64_t plane = (int64_t)f->nu * f->nv;
   const int fwd = sign < 0 ? 1 : 0;
-  // rows (length nv, contiguous): doubles -> df64
-  {
-    size_t smem = 2 * sizeof(float4) * (size_t)f->lines_v * f->nv;
-    cudaError_t e = cudaFuncSetAttribute(k_fft_lines, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kFftSmem);
+  const bool prune = keep_rows > 0 && keep_rows < f->nu;
+  if (prune && (keep_rows & 1)) return cudaErrorInvalidValue;
+  const int half = prune ? (int)(keep_rows / 2) : f->nu;
+  const int skip = prune ? f->nu - (int)keep_rows : 0;
+  const int nrows = prune ? (int)keep_rows : f->nu;
+  cudaError_t e;
+  if (!prune || fwd) {
+    // rows (length nv, contiguous): doubles -> df64; then columns (length nu, stride nv):
+    // df64 -> doubles
+    e = launch_lines(f->lv, data, batch, plane, nrows, f->nv, 1, 0, fwd, half, skip, s);
     if (e != cudaSuccess) return e;
-    int64_t blocks = batch * (f->nu / f->lines_v);
-    k_fft_lines<<<(unsigned)blocks, 256, smem, s>>>(f->lv, data, plane, f->nu, f->lines_v,
-                                                     (int64_t)f->nv, 1, 0, fwd);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    return launch_lines(f->lu, data, batch, plane, f->nv, 1, f->nv, 1, fwd, f->nv, 0, s);
   }
-  // columns (length nu, stride nv): df64 -> doubles
-  {
-    size_t smem = 2 * sizeof(float4) * (size_t)f->lines_u * f->nu;
-    int64_t blocks = batch * (f->nv / f->lines_u);
-    k_fft_lines<<<(unsigned)blocks, 256, smem, s>>>(f->lu, data, plane, f->nv, f->lines_u, 1,
-                                                     (int64_t)f->nv, 1, fwd);
-    return cudaGetLastError();
-  }
+  // pruned inverse: columns doubles -> df64, then the kept rows df64 -> doubles
+  e = launch_lines(f->lu, data, batch, plane, f->nv, 1, f->nv, 0, fwd, f->nv, 0, s);
+  if (e != cudaSuccess) return e;
+  return launch_lines(f->lv, data, batch, plane, nrows, f->nv, 1, 1, fwd, half, skip, s);
 }
 
 }  // namespace wg

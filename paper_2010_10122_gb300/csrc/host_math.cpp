@@ -256,41 +256,136 @@ int64_t good_size(int64_t n, int64_t mult) {
   return q * mult;
 }
 
-// Measured cuFFT plane times on GB300 (batched 2-D C2C / Z2Z), written by calibrate_fft.py.
+bool df64_line_plan(int64_t n, Df64LinePlan* lp) {
+  if (n < 2 || n > kDf64MaxSide) return false;
+  int k = 0;
+  int64_t m = n;
+  int p2 = 0;
+  while (m % 2 == 0) { m /= 2; ++p2; }
+  if (p2 == 1) {
+    lp->radix[k++] = 2;
+  } else {
+    int e8 = p2 / 3, rem = p2 % 3;
+    if (rem == 1) --e8;                  // 2^(3q+1) = 8^(q-1) * 4 * 4 (q >= 1 since p2 >= 4)
+    for (int i = 0; i < e8; ++i) lp->radix[k++] = 8;
+    if (rem == 1) { lp->radix[k++] = 4; lp->radix[k++] = 4; }
+    if (rem == 2) lp->radix[k++] = 4;
+  }
+  for (int p : {5, 3, 7, 11})
+    while (m % p == 0 && k < 24) { lp->radix[k++] = p; m /= p; }
+  if (m != 1) return false;
+  lp->nst = k;
+  lp->threads = (int)std::max<int64_t>(64, (n / 8 + 31) / 32 * 32);
+  return lp->threads <= 832;
+}
+
+bool df64_side_ok(int64_t n) {
+  Df64LinePlan lp;
+  return df64_line_plan(n, &lp);
+}
+
+double rounding_gain(const PolyKernel& K, const std::vector<double>& psi_c, int64_t nx,
+                     int64_t ny, double psx, double psy, int64_t nu, int64_t nv, int do_w,
+                     double nshift, double dw) {
+  // int phi^2 over the support, Gauss-Legendre per piece (the integrand is a polynomial)
+  static thread_local std::vector<double> gx, gw;
+  if (gx.empty()) gauss_legendre(32, gx, gw);
+  long double phi2 = 0.0L;
+  for (int i = 0; i < K.alpha; ++i)
+    for (size_t q = 0; q < gx.size(); ++q) {
+      double v = K.eval_piece(i, gx[q]);
+      phi2 += (long double)(0.5 * gw[q]) * v * v;
+    }
+  // rms of the correction over a midpoint lattice of pixels
+  const int su = (int)std::min<int64_t>(nx, 64), sv = (int)std::min<int64_t>(ny, 64);
+  std::vector<double> jx(su), jy(sv), iu(su), iv(sv);
+  for (int a = 0; a < su; ++a) {
+    jx[a] = -0.5 * nx + (a + 0.5) * (double)nx / su;
+    iu[a] = 1.0 / psi_cheb_eval(psi_c, jx[a] / nu);
+  }
+  for (int b = 0; b < sv; ++b) {
+    jy[b] = -0.5 * ny + (b + 0.5) * (double)ny / sv;
+    iv[b] = 1.0 / psi_cheb_eval(psi_c, jy[b] / nv);
+  }
+  long double acc = 0.0L;
+  for (int a = 0; a < su; ++a)
+    for (int b = 0; b < sv; ++b) {
+      double l = jx[a] * psx, m = jy[b] * psy;
+      double r2 = l * l + m * m;
+      double n = std::sqrt(std::max(0.0, 1.0 - r2));
+      double c = iu[a] * iv[b] / n;
+      if (do_w) {
+        double nm1 = -r2 / (1.0 + n);
+        c /= psi_cheb_eval(psi_c, (nm1 - nshift) * dw);
+      }
+      acc += (long double)c * c;
+    }
+  double rms = std::sqrt((double)(acc / ((long double)su * sv)));
+  return rms * std::pow((double)phi2, do_w ? 1.5 : 1.0);
+}
+
+double plane_rounding(int kind, int prec, int64_t nu, int64_t nv) {
+  // unit roundoff of the plane arithmetic.  c: on GB300 (2048^2 image, 1e6 visibilities,
+  // alpha 16, sigma 1.5 - 2.0, gain 880 - 2.7) the double-float planes added a degrid error of
+  // (4.0 - 6.1)e-15 x gain, i.e. c = 0.024 - 0.037 at 3200^2; 0.06 leaves a margin
+  double u = kind == kFftDf64 ? 0x1p-47 : (prec ? 0x1p-53 : 0x1p-24);
+  const double c = 0.06;
+  return c * u * std::log2((double)nu * (double)nv);
+}
+
+// Measured plane-transform times on GB300, written by calibrate_fft.py: batched cuFFT 2-D C2C
+// and Z2Z, and the library's double-float FFT (0 where it does not support the size).
 struct FftRow {
   int64_t n;
-  double ms32, ms64;
+  double ms32, ms64, msdf;
 };
 static const FftRow kFftTable[] = {
 #include "fft_table.inc"
 };
 static const size_t kFftRows = sizeof(kFftTable) / sizeof(kFftTable[0]);
 
-// Milliseconds of one n x n plane transform: the table value, else an n^2 log n extrapolation
-// from the largest measured size.
-static double fft_ms_square(int64_t n, int prec) {
-  for (size_t i = 0; i < kFftRows; ++i)
-    if (kFftTable[i].n == n) return prec ? kFftTable[i].ms64 : kFftTable[i].ms32;
-  const FftRow& L = kFftTable[kFftRows - 1];
-  double ref = prec ? L.ms64 : L.ms32;
-  double a = (double)n * n * std::log2((double)n * n), b = (double)L.n * L.n * std::log2((double)L.n * L.n);
-  return ref * a / b * 1.3;   // unmeasured sizes are priced a little higher
+static double row_ms(const FftRow& r, int kind, int prec) {
+  if (kind == kFftDf64) return r.msdf;
+  return prec ? r.ms64 : r.ms32;
 }
 
-// Rectangular nu x nv plane: per-cell cost averaged over the two axis lengths.
-static double fft_ms(int64_t nu, int64_t nv, int prec) {
-  double cu = fft_ms_square(nu, prec) / ((double)nu * nu);
-  double cv = fft_ms_square(nv, prec) / ((double)nv * nv);
-  return 0.5 * (cu + cv) * (double)nu * nv;
+// Milliseconds of one n x n plane transform of the given kind: the table value, else an
+// n^2 log n extrapolation from the largest measured size.
+static double fft_ms_square(int64_t n, int kind, int prec) {
+  for (size_t i = 0; i < kFftRows; ++i)
+    if (kFftTable[i].n == n && row_ms(kFftTable[i], kind, prec) > 0) return row_ms(kFftTable[i], kind, prec);
+  for (size_t i = kFftRows; i-- > 0;) {
+    const FftRow& L = kFftTable[i];
+    double ref = row_ms(L, kind, prec);
+    if (ref <= 0) continue;
+    double a = (double)n * n * std::log2((double)n * n), b = (double)L.n * L.n * std::log2((double)L.n * L.n);
+    return ref * a / b * 1.3;   // unmeasured sizes are priced a little higher
+  }
+  return std::numeric_limits<double>::infinity();
 }
+
+// One nu x nv plane of the given kind: per-cell cost averaged over the two axis lengths; the
+// pruned kinds transform only the nx image rows in one of their two passes.
+static double fft_ms(int64_t nu, int64_t nv, int kind, int prec, int64_t nx) {
+  double cu = fft_ms_square(nu, kind, prec) / ((double)nu * nu);
+  double cv = fft_ms_square(nv, kind, prec) / ((double)nv * nv);
+  double full = 0.5 * (cu + cv) * (double)nu * nv;
+  double rows = 0.5 + 0.5 * std::min(1.0, (double)nx / (double)nu);
+  if (kind == kFftPrunedZ2Z) return full * rows * 1.07;   // 1-D plans: measured 7 % overhead
+  if (kind == kFftDf64) return full * rows;
+  return full;
+}
+
+static bool kind_supports(int kind, int64_t n) { return kind != kFftDf64 || df64_side_ok(n); }
 
 // Grid-size candidates >= nmin: the next measured sizes (multiples of `mult`), or FFT-friendly
 // sizes beyond the table.
-static std::vector<int64_t> size_candidates(int64_t nmin, int64_t mult) {
+static std::vector<int64_t> size_candidates(int64_t nmin, int64_t mult, int kind) {
   std::vector<int64_t> c;
   for (size_t i = 0; i < kFftRows && c.size() < 10; ++i)
-    if (kFftTable[i].n >= nmin && kFftTable[i].n % mult == 0) c.push_back(kFftTable[i].n);
-  if (c.empty()) c.push_back(good_size(nmin, mult));
+    if (kFftTable[i].n >= nmin && kFftTable[i].n % mult == 0 && kind_supports(kind, kFftTable[i].n))
+      c.push_back(kFftTable[i].n);
+  if (c.empty() && kind != kFftDf64) c.push_back(good_size(nmin, mult));
   return c;
 }
 
@@ -298,26 +393,28 @@ static std::vector<int64_t> size_candidates(int64_t nmin, int64_t mult) {
 // per cell and the w-screen phase per image pixel; per visibility the alpha^3 (de)gridding
 // work.  The per-cell / per-pixel / per-visibility constants are measured stage times of this
 // library on GB300 (2048^2 image, 1e6 visibilities) divided by the units processed.
-static double plan_cost(int prec, int64_t nu, int64_t nv, int64_t nw, int alpha, int64_t nvis,
-                        int64_t npix) {
+static double plan_cost(int prec, int kind, int64_t nu, int64_t nv, int64_t nw, int alpha,
+                        int64_t nvis, int64_t nx, int64_t npix) {
   double cells = (double)nu * nv;
   double k_cell = prec ? 3.0e-12 : 2.5e-12;   // s per plane cell (screen / (de)grid traffic)
   double k_pix = prec ? 6.0e-11 : 1.8e-12;    // s per image pixel per plane (screen phase)
   double k_vis = prec ? 1.05e-11 : 5.0e-12;   // s per visibility per alpha^3
-  return nw * (1e-3 * fft_ms(nu, nv, prec) + cells * k_cell + (double)npix * k_pix) +
+  return nw * (1e-3 * fft_ms(nu, nv, kind, prec, nx) + cells * k_cell + (double)npix * k_pix) +
          (double)nvis * alpha * alpha * alpha * k_vis;
 }
 
-// Cheapest (nu, nv) for one plane among the candidates (FFT + traffic per cell).
-static void choose_grid(int64_t nmin_u, int64_t nmin_v, int prec, int64_t mult, int64_t* nu,
-                        int64_t* nv) {
+// Cheapest (nu, nv) for one plane among the candidates (FFT + traffic per cell); false if the
+// FFT kind supports none.
+static bool choose_grid(int64_t nmin_u, int64_t nmin_v, int prec, int kind, int64_t mult,
+                        int64_t nx, int64_t* nu, int64_t* nv) {
   double k_cell = prec ? 3.0e-12 : 2.5e-12;
   double best = std::numeric_limits<double>::infinity();
-  for (int64_t a : size_candidates(nmin_u, mult))
-    for (int64_t b : size_candidates(nmin_v, mult)) {
-      double c = 1e-3 * fft_ms(a, b, prec) + k_cell * (double)a * b;
+  for (int64_t a : size_candidates(nmin_u, mult, kind))
+    for (int64_t b : size_candidates(nmin_v, mult, kind)) {
+      double c = 1e-3 * fft_ms(a, b, kind, prec, nx) + k_cell * (double)a * b;
       if (c < best) { best = c; *nu = a; *nv = b; }
     }
+  return std::isfinite(best);
 }
 
 int choose_plan(const PlanInput& in, PlanParams& out, char* err, int errlen) {
@@ -330,6 +427,9 @@ int choose_plan(const PlanInput& in, PlanParams& out, char* err, int errlen) {
   if (!(in.psx > 0) || !(in.psy > 0)) return fail("pixel sizes must be positive");
   if (!(in.eps > 2e-13)) return fail("epsilon must be larger than 2e-13");
   if (in.prec == 0 && in.eps < 1e-5) return fail("single precision requires epsilon >= 1e-5");
+  if (in.fft_impl < 0 || in.fft_impl > 3) return fail("fft_impl must be 0, 1, 2 or 3");
+  if (in.prec == 0 && (in.fft_impl == kFftDf64 || in.fft_impl == kFftPrunedZ2Z))
+    return fail("fft_impl 2 and 3 need WG_F64");
   // most negative n - 1 over the image: the corner pixel (-nx/2, -ny/2) (Sec. 2, sets L, M)
   double lmax = 0.5 * in.nx * in.psx, mmax = 0.5 * in.ny * in.psy;
   double r2 = lmax * lmax + mmax * mmax;
@@ -337,8 +437,15 @@ int choose_plan(const PlanInput& in, PlanParams& out, char* err, int errlen) {
   double nm1_min = -r2 / (1.0 + std::sqrt(1.0 - r2));
   if (in.tile != 0 && in.tile != 16 && in.tile != 32) return fail("tile must be 16 or 32");
 
+  // FFT kinds to consider: FP32 plans use cuFFT C2C; FP64 plans the pruned Z2Z transform or the
+  // double-float FFT, whichever is cheaper among those whose rounding fits epsilon
+  std::vector<int> kinds;
+  if (in.fft_impl != 0) kinds.push_back(in.fft_impl);
+  else if (in.prec == 0) kinds.push_back(kFftCufft2d);
+  else { kinds.push_back(kFftPrunedZ2Z); kinds.push_back(kFftDf64); }
+
   double safety = in.eps_safety > 0 ? in.eps_safety : kDefaultEpsSafety;
-  bool found = false;
+  bool found = false, size_ok = false;
   PlanParams best;
   best.cost = std::numeric_limits<double>::infinity();
   const auto& T = kernel_table();
@@ -348,52 +455,75 @@ int choose_plan(const PlanInput& in, PlanParams& out, char* err, int errlen) {
     // area would otherwise crowd shared memory
     int tile = in.tile > 0 ? in.tile : ((in.prec == 1 && alpha >= 12) ? 16 : 32);
     if (alpha - 1 > tile) continue;
-    // Sec. 4.1: for each alpha the smallest sigma whose kernel meets epsilon
-    const KernelRow* pick = nullptr;
+    std::vector<const KernelRow*> rows;
     for (const auto& r : T) {
       if (r.alpha != alpha) continue;
       if (in.force_sigma > 0 && std::fabs(r.sigma - in.force_sigma) > 1e-9) continue;
-      if (r.eps <= in.eps * safety && (!pick || r.sigma < pick->sigma)) pick = &r;
+      if (r.eps <= in.eps * safety) rows.push_back(&r);
     }
-    if (!pick) continue;
-    PlanParams p;
-    p.alpha = alpha; p.sigma = pick->sigma; p.beta = pick->beta; p.mu = pick->mu;
-    p.eps_kernel = pick->eps;
-    p.tile = tile;
-    // Sec. 2: N >= ceil(sigma n); among the FFT-friendly multiples of the tile above it the
-    // one with the cheapest measured plane transform
-    int64_t minn = std::max<int64_t>(2 * alpha, 16);
-    choose_grid(std::max<int64_t>((int64_t)std::ceil(p.sigma * in.nx), minn),
-                std::max<int64_t>((int64_t)std::ceil(p.sigma * in.ny), minn), in.prec, tile,
-                &p.nu, &p.nv);
-    p.ntu = p.nu / tile; p.ntv = p.nv / tile;
-    p.nm1_min = nm1_min;
-    if (in.do_w) {
-      double span;  // extent of the n - 1 values the w-kernel must resolve
-      if (in.w_shift) {
-        p.nshift = 0.5 * nm1_min;   // centre of [nm1_min, 0]
-        span = 0.5 * std::fabs(nm1_min);
-      } else {
-        p.nshift = 0.0;
-        span = std::fabs(nm1_min);
+    std::sort(rows.begin(), rows.end(),
+              [](const KernelRow* a, const KernelRow* b) { return a->sigma < b->sigma; });
+    for (int kind : kinds) {
+      // Sec. 4.1: for each alpha the smallest sigma whose kernel meets epsilon -- here the
+      // kernel term together with the plane rounding of this FFT kind (unless sigma is forced)
+      for (const KernelRow* pick : rows) {
+        PlanParams p;
+        p.alpha = alpha; p.sigma = pick->sigma; p.beta = pick->beta; p.mu = pick->mu;
+        p.eps_kernel = pick->eps;
+        p.tile = tile;
+        p.fft_kind = kind;
+        // Sec. 2: N >= ceil(sigma n); among the FFT-friendly multiples of the tile above it
+        // the one with the cheapest measured plane transform
+        int64_t minn = std::max<int64_t>(2 * alpha, 16);
+        if (!choose_grid(std::max<int64_t>((int64_t)std::ceil(p.sigma * in.nx), minn),
+                         std::max<int64_t>((int64_t)std::ceil(p.sigma * in.ny), minn), in.prec,
+                         kind, tile, in.nx, &p.nu, &p.nv))
+          break;   // larger sigma only needs larger grids
+        size_ok = true;
+        p.ntu = p.nu / tile; p.ntv = p.nv / tile;
+        p.nm1_min = nm1_min;
+        if (in.do_w) {
+          double span;  // extent of the n - 1 values the w-kernel must resolve
+          if (in.w_shift) {
+            p.nshift = 0.5 * nm1_min;   // centre of [nm1_min, 0]
+            span = 0.5 * std::fabs(nm1_min);
+          } else {
+            p.nshift = 0.0;
+            span = std::fabs(nm1_min);
+          }
+          // Sec. 2: Delta w = 1 / (2 sigma max |n - 1|) (Nyquist), with the maximum taken over
+          // the n - 1 values relative to the reference nshift
+          p.dw = 1.0 / (2.0 * p.sigma * span);
+          double wmin = in.wmin, wmax = std::max(in.wmax, in.wmin);
+          // Eq. (wcirc): first plane half a kernel width below the smallest w
+          p.w0 = wmin - 0.5 * p.dw * (alpha - 1);
+          // N_w = (max w - min w) / Delta w + alpha, rounded up, plus one plane of slack for
+          // rounding in the per-visibility plane index
+          p.nw = (int64_t)std::ceil((wmax - wmin) / p.dw) + alpha + 1;
+        } else {
+          p.nshift = 0.0; p.dw = 1.0; p.w0 = 0.0; p.nw = 1;
+        }
+        if (p.nw > 4095) break;  // plane index must fit 12 bits (FP32 phase split)
+        PolyKernel K = make_poly_kernel(alpha, p.beta, p.mu, alpha + 3);
+        std::vector<double> pc = psi_cheb_coeffs(K, kPsiChebTerms);
+        p.gain = rounding_gain(K, pc, in.nx, in.ny, in.psx, in.psy, p.nu, p.nv, in.do_w,
+                               p.nshift, p.dw);
+        double e_k = p.eps_kernel / safety;
+        double e_r = plane_rounding(kind, in.prec, p.nu, p.nv) * p.gain;
+        p.err_model = std::sqrt(e_k * e_k + e_r * e_r);
+        if (in.force_sigma <= 0 && p.err_model > in.eps) continue;
+        p.cost = plan_cost(in.prec, kind, p.nu, p.nv, p.nw, alpha, in.nvis, in.nx,
+                           in.nx * in.ny);
+        if (p.cost < best.cost) { best = p; found = true; }
+        break;
       }
-      // Sec. 2: Delta w = 1 / (2 sigma max |n - 1|) (Nyquist), with the maximum taken over
-      // the n - 1 values relative to the reference nshift
-      p.dw = 1.0 / (2.0 * p.sigma * span);
-      double wmin = in.wmin, wmax = std::max(in.wmax, in.wmin);
-      // Eq. (wcirc): first plane half a kernel width below the smallest w
-      p.w0 = wmin - 0.5 * p.dw * (alpha - 1);
-      // N_w = (max w - min w) / Delta w + alpha, rounded up, plus one plane of slack for
-      // rounding in the per-visibility plane index
-      p.nw = (int64_t)std::ceil((wmax - wmin) / p.dw) + alpha + 1;
-    } else {
-      p.nshift = 0.0; p.dw = 1.0; p.w0 = 0.0; p.nw = 1;
     }
-    if (p.nw > 4095) continue;  // plane index must fit 12 bits (FP32 phase split)
-    p.cost = plan_cost(in.prec, p.nu, p.nv, p.nw, alpha, in.nvis, in.nx * in.ny);
-    if (p.cost < best.cost) { best = p; found = true; }
   }
-  if (!found) return fail("no kernel in the table meets the requested epsilon");
+  if (!found) {
+    if (!size_ok && in.fft_impl == kFftDf64)
+      return fail("the double-float FFT supports grid sides up to 6400 only");
+    return fail("no kernel in the table meets the requested epsilon");
+  }
   out = best;
   return 0;
 }

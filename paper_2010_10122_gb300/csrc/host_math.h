@@ -51,6 +51,38 @@ void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
 // factor above 7 (FFT-friendly sizes for cuFFT).
 int64_t good_size(int64_t n, int64_t mult);
 
+// Plane FFT implementations.
+enum FftKind { kFftCufft2d = 1, kFftDf64 = 2, kFftPrunedZ2Z = 3 };
+// The double-float FFT keeps two lines of n complex df64 values in shared memory per CTA
+// (200 KB): sides up to 6400 whose prime factors are 2, 3, 5, 7 and 11.
+constexpr int64_t kDf64MaxSide = 6400;
+// Radix plan and CTA size of one double-float line transform: radices 8 and 4 for the power
+// of two (2 only for n = 2 * odd), then 5, 3, 7, 11; n / 8 threads rounded up to a warp
+// multiple (at least 64).
+struct Df64LinePlan {
+  int nst = 0, threads = 0;
+  int radix[24];
+};
+bool df64_line_plan(int64_t n, Df64LinePlan* plan);
+bool df64_side_ok(int64_t n);
+
+// Gain of plane rounding into the result.  A plane value perturbed by a relative (normwise)
+// rounding delta reaches the degridded visibilities / gridded image through the kernel
+// footprint and the correction 1 / (n psi_u psi_v psi_w) of Eqs. R1 / Rad1; for an image with
+// uniformly spread flux the relative error of the result is delta * G with
+//   G = rms over the image of 1 / (n psi_u psi_v psi_w)  *  (int phi^2 dx)^(d / 2),
+// d = 3 with w-stacking (2 without): the rms per cell of an unnormalised FFT of I * corr is
+// ||I * corr||, and the footprint sums alpha cells per axis with weights phi.  Evaluated on a
+// lattice of at most 64 x 64 pixel samples.
+double rounding_gain(const PolyKernel& K, const std::vector<double>& psi_c, int64_t nx,
+                     int64_t ny, double psx, double psy, int64_t nu, int64_t nv, int do_w,
+                     double nshift, double dw);
+
+// Relative normwise rounding of one plane transform (and the arithmetic around it) of the
+// given kind and precision on an nu x nv grid: c * u * log2(nu nv), with u the unit roundoff
+// (FP32 2^-24, FP64 2^-53, double-float 2^-47) and c fitted on GB300 measurements.
+double plane_rounding(int kind, int prec, int64_t nu, int64_t nv);
+
 struct PlanInput {
   int64_t nx, ny;
   double psx, psy;
@@ -63,6 +95,7 @@ struct PlanInput {
   int tile;
   double umax, vmax, wmin, wmax;  // wavelengths (|u|, |v| maxima, |w| range)
   int64_t nvis;
+  int fft_impl = 0;  // requested plane FFT: 0 automatic, else an FftKind
 };
 
 struct PlanParams {
@@ -75,6 +108,9 @@ struct PlanParams {
   int tile = 0;
   int64_t ntu = 0, ntv = 0;
   double cost = 0;
+  int fft_kind = kFftCufft2d;
+  double gain = 0;       // rounding_gain of the plan
+  double err_model = 0;  // predicted eps_rms: kernel term (+) plane rounding term
 };
 
 // Returns 0 on success; on failure fills err (WG_ERR_ARG class problems).

@@ -184,21 +184,67 @@ __global__ void k_degrid_finalize(const Geom g, const IndexView<R> ix,
 // CTA = (uv tile, sub-batch of bs planes).  Warp w owns planes w, w + 8, ... of the
 // sub-batch: it alone updates their T x T accumulators, so the updates are plain shared-memory
 // read-modify-writes (no atomics, deterministic order).  Visibilities are handled in chunks:
-// first every thread group computes the chunk's kernel weights (alpha values in u, v and w,
-// Horner, Sec. 4.2) and weighted data into shared memory; then each warp walks the chunk and,
-// for every visibility touching one of its planes, its 32 lanes cover distinct cells of the
-// alpha x alpha footprint (lane -> column j, row group rg; rows rg, rg + 32/G, ...).
+// first a group of G lanes per visibility stages its kernel values in u and v (Sec. 4.2) and
+// its data times the w kernel value of each of its planes; then each warp walks the chunk and,
+// for every visibility touching one of its planes, spreads the 32 lanes over the cells of the
+// footprint that fall inside the tile (the clipped footprint, row-major), computes their 2-D
+// weights wu * wv once, and adds them into each of its planes the visibility touches.
 // ---------------------------------------------------------------------------------------
 constexpr int kChunk = 64;   // visibilities staged per chunk
+constexpr int kOwnerWarps = kThreads / 32;   // warp w owns planes w, w + kOwnerWarps, ...
 
 template <typename R>
 struct GridStage {
   R wu[kChunk][kMaxG];
   R wv[kChunk][kMaxG];
-  R ww[kChunk][kMaxG];
-  typename C2<R>::T d[kChunk];
+  typename C2<R>::T dq[kChunk][kMaxG];   // data x w kernel value of plane q of the visibility
   int ru[kChunk], rv[kChunk], c0[kChunk];
 };
+
+// The part of a visibility's footprint inside the tile: rows i0.., columns j0..j0 + w - 1 of
+// the footprint, `cells` cells in all, footprint origin at tile cell (ru, rv).
+struct OwnerFootprint {
+  int i0, j0, w, cells, ru, rv;
+};
+
+// Add visibility v of the chunk into the warp's planes p1, p1 + kOwnerWarps, .. < phi: lane
+// takes cells lane + 32 m (m < MC) of the clipped footprint in row-major order, forms their
+// 2-D weights once and updates each plane (plane pl uses the staged data x w value of the
+// visibility's plane pl + qoff).  Lanes past the last cell update a private cell of the row
+// padding (columns T, T + 1) with weight 0, so every update is unconditional.
+template <typename R, int MC>
+__device__ __forceinline__ void owner_add(const GridStage<R>* __restrict__ stg, int v,
+                                          const OwnerFootprint& fp, int lane, int T, int pitch,
+                                          int p1, int phi, int qoff,
+                                          typename C2<R>::T* __restrict__ acc, int plane_elems) {
+  using CT = typename C2<R>::T;
+  const float rw = 1.0f / (float)fp.w;
+  const int dummy = (lane >> 1) * pitch + T + (lane & 1);
+  R wt[MC];
+  int off[MC];
+#pragma unroll
+  for (int m = 0; m < MC; ++m) {
+    const int c = lane + 32 * m;
+    // c = ii * w + jj; exact in float: c < 256 and w <= 16 keep (c + 0.5) / w at least 1 / 32
+    // away from an integer
+    const int ii = (int)(((float)c + 0.5f) * rw), jj = c - ii * fp.w;
+    const bool ok = c < fp.cells;
+    const int i = fp.i0 + (ok ? ii : 0), j = fp.j0 + (ok ? jj : 0);
+    wt[m] = ok ? stg->wu[v][i] * stg->wv[v][j] : (R)0;
+    off[m] = ok ? (fp.ru + i) * pitch + fp.rv + j : dummy;
+  }
+  for (int pl = p1; pl < phi; pl += kOwnerWarps) {
+    const CT dq = stg->dq[v][pl + qoff];
+    CT* base = acc + pl * plane_elems;
+#pragma unroll
+    for (int m = 0; m < MC; ++m) {
+      CT a = base[off[m]];
+      a.x = fma(dq.x, wt[m], a.x);
+      a.y = fma(dq.y, wt[m], a.y);
+      base[off[m]] = a;
+    }
+  }
+}
 
 template <typename R, int G>
 __global__ void __launch_bounds__(kThreads)
@@ -221,12 +267,10 @@ k_grid_owner(const Geom g, const __grid_constant__ Coef<R> coef, const IndexView
     CT z; z.x = (R)0; z.y = (R)0;
     acc[e] = z;
   }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // phase-1 mapping: groups of G lanes, one visibility each
   const int j1 = threadIdx.x & (G - 1), grp = threadIdx.x / G, ngrp = blockDim.x / G;
-  // phase-2 mapping: lane -> column jc, first row rg; rows advance by 32 / G
-  const int jc = lane & (G - 1), rg = lane / G;
-  constexpr int RSTEP = 32 / G;
+  const unsigned gmask = group_mask<G>();
 
   for (int src = 0; src < 4; ++src) {
     const int ou = (src & 1) ? -1 : 0, ov = (src & 2) ? -1 : 0;
@@ -237,7 +281,7 @@ k_grid_owner(const Geom g, const __grid_constant__ Coef<R> coef, const IndexView
     for (uint32_t cs = lo; cs < hi; cs += kChunk) {
       const int nch = (int)min((uint32_t)kChunk, hi - cs);
       __syncthreads();  // previous chunk consumed (and accumulators zeroed)
-      // ---- phase 1: weights and data of the chunk ----
+      // ---- phase 1: kernel values and plane-weighted data of the chunk ----
       for (int v = grp; v < nch; v += ngrp) {
         const uint32_t vi = cs + v;
         const uint32_t mt = ix.meta[vi];
@@ -247,18 +291,19 @@ k_grid_owner(const Geom g, const __grid_constant__ Coef<R> coef, const IndexView
           stg->ru[v] = ru; stg->rv[v] = rv;
           stg->c0[v] = hit ? (int)(mt >> 16) : -(1 << 20);
         }
-        if (!hit) continue;
+        if (!hit) continue;   // uniform within the group
         const Z4<R> zz = ix.z[vi];
         const bool lj = j1 < alpha;
         stg->wu[v][j1] = lj ? kernel_value(ix, sc, g.deg, vi, 0, j1, zz.u) : (R)0;
         stg->wv[v][j1] = lj ? kernel_value(ix, sc, g.deg, vi, 1, j1, zz.v) : (R)0;
-        stg->ww[v][j1] = g.do_w ? (lj ? kernel_value(ix, sc, g.deg, vi, 2, j1, zz.w) : (R)0)
-                                : (j1 == 0 ? (R)1 : (R)0);
+        const R wwj = g.do_w ? (lj ? kernel_value(ix, sc, g.deg, vi, 2, j1, zz.w) : (R)0)
+                             : (j1 == 0 ? (R)1 : (R)0);
+        R dr = (R)0, di = (R)0;
         if (j1 == 0) {
           const uint32_t id = ix.idx[vi];
           const int64_t k = id & ~kFoldBit;
           CT d = vis[k];
-          R dr = d.x, di = d.y;
+          dr = d.x; di = d.y;
           if (wgt != nullptr) { R w = wgt[k]; dr *= w; di *= w; }
           if (id & kFoldBit) di = -di;      // grid conj(d) at the folded coordinates
           if (ix.ph != nullptr) {           // times conj(exp(2 pi i w nshift))
@@ -267,39 +312,38 @@ k_grid_owner(const Geom g, const __grid_constant__ Coef<R> coef, const IndexView
             di = di * ph.x - dr * ph.y;
             dr = r;
           }
-          CT o; o.x = dr; o.y = di;
-          stg->d[v] = o;
         }
+        dr = __shfl_sync(gmask, dr, 0, G);
+        di = __shfl_sync(gmask, di, 0, G);
+        CT o; o.x = dr * wwj; o.y = di * wwj;
+        stg->dq[v][j1] = o;
       }
       __syncthreads();
       // ---- phase 2: each warp adds the chunk into its own planes ----
       for (int v = 0; v < nch; ++v) {
         const int c0 = stg->c0[v];
         if (c0 < -1000) continue;
+        // this warp's planes among the visibility's planes c0 .. c0 + aw - 1
+        const int plo = max(0, c0 - s0), phi = min(sb, c0 - s0 + aw);
+        const int p1 = plo + ((warp - plo) & (kOwnerWarps - 1));
+        if (p1 >= phi) continue;
         const int ru = stg->ru[v], rv = stg->rv[v];
-        const int col = rv + jc;
-        const bool colok = jc < alpha && col >= 0 && col < T;
-        const CT d = stg->d[v];
-        const R wvj = stg->wv[v][jc];
-        for (int pl = warp; pl < sb; pl += nwarps) {
-          const int q = s0 + pl - c0;
-          if (q < 0 || q >= aw) continue;
-          if (!colok) continue;
-          const R wq = stg->ww[v][q] * wvj;
-          const R dr = d.x * wq, di = d.y * wq;
-          CT* base = acc + pl * plane_elems + col;
-#pragma unroll
-          for (int m = 0; m < (G + RSTEP - 1) / RSTEP; ++m) {
-            const int i = rg + m * RSTEP;
-            const int row = ru + i;
-            if (i < alpha && row >= 0 && row < T) {
-              const R wui = stg->wu[v][i];
-              CT a = base[row * pitch];
-              a.x = fma(dr, wui, a.x);
-              a.y = fma(di, wui, a.y);
-              base[row * pitch] = a;
-            }
-          }
+        // footprint rows i0..i1-1 and columns j0..j1-1 inside the tile
+        const int i0 = max(0, -ru), i1 = min(alpha, T - ru);
+        const int j0 = max(0, -rv), j1c = min(alpha, T - rv);
+        const int w = j1c - j0, cells = (i1 - i0) * w;
+        // dispatch on the warp-uniform number of cells per lane, so that each case runs
+        // exactly its updates (no predicated-off FP64 instructions)
+        const OwnerFootprint fp{i0, j0, w, cells, ru, rv};
+        switch ((cells + 31) >> 5) {
+          case 1: owner_add<R, 1>(stg, v, fp, lane, T, pitch, p1, phi, s0 - c0, acc, plane_elems); break;
+          case 2: owner_add<R, 2>(stg, v, fp, lane, T, pitch, p1, phi, s0 - c0, acc, plane_elems); break;
+          case 3: owner_add<R, (G > 8 ? 3 : 1)>(stg, v, fp, lane, T, pitch, p1, phi, s0 - c0, acc, plane_elems); break;
+          case 4: owner_add<R, (G > 8 ? 4 : 1)>(stg, v, fp, lane, T, pitch, p1, phi, s0 - c0, acc, plane_elems); break;
+          case 5: owner_add<R, (G > 8 ? 5 : 1)>(stg, v, fp, lane, T, pitch, p1, phi, s0 - c0, acc, plane_elems); break;
+          case 6: owner_add<R, (G > 8 ? 6 : 1)>(stg, v, fp, lane, T, pitch, p1, phi, s0 - c0, acc, plane_elems); break;
+          case 7: owner_add<R, (G > 8 ? 7 : 1)>(stg, v, fp, lane, T, pitch, p1, phi, s0 - c0, acc, plane_elems); break;
+          default: owner_add<R, (G > 8 ? 8 : 1)>(stg, v, fp, lane, T, pitch, p1, phi, s0 - c0, acc, plane_elems); break;
         }
       }
     }
@@ -498,8 +542,10 @@ template <typename R, int G>
 static cudaError_t grid_owner_g(const Geom& g, const Coef<R>& coef, const IndexView<R>& ix,
                                 const typename C2<R>::T* vis, const R* wgt,
                                 typename C2<R>::T* planes, int b0, int nb, cudaStream_t s) {
-  // accumulator rows padded so that the row groups of a warp fall on different banks (FP32)
-  const int pitch = g.tile + (sizeof(R) == 4 ? 8 : 0);
+  // accumulator rows padded by two cells: rows of a clipped footprint start on different
+  // banks, and the 2 x T padding cells of a plane give each lane of its owner warp a private
+  // cell for idle updates
+  const int pitch = g.tile + 2;
   const size_t per = (size_t)g.tile * pitch * sizeof(typename C2<R>::T);
   const size_t fixed = coef_bytes<R>() + sizeof(GridStage<R>);
   const int nwarps = kThreads / 32;

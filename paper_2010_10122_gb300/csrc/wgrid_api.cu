@@ -297,6 +297,7 @@ static PlanInput plan_input(int64_t npix_x, int64_t npix_y, double psx, double p
   in.do_w = o.do_wstacking; in.w_shift = o.w_shift; in.eps_safety = o.eps_safety;
   in.force_alpha = o.force_alpha; in.force_sigma = o.force_sigma; in.tile = o.tile;
   in.umax = umax; in.vmax = vmax; in.wmin = wmin; in.wmax = wmax; in.nvis = nvis;
+  in.fft_impl = o.fft_impl;
   return in;
 }
 
@@ -422,15 +423,12 @@ int wg_plan_create(const double* uvw, const double* freq, int64_t nrows, int64_t
     p->index_bytes += tb;
   }
 
-  // plane FFTs: the double-float FFT for FP64 planes it supports, cuFFT otherwise
-  const int fft_impl = p->opt.fft_impl;
-  if (fft_impl < 0 || fft_impl > 3) return fail(set_error(WG_ERR_ARG, "fft_impl must be 0, 1, 2 or 3"));
-  // automatic: the double-float FFT's rounding (~5e-15 normwise) is amplified by 1 / psi at the
-  // image edge to ~1e-12 of the result, so it serves FP64 plans with epsilon >= 1e-11 only
-  bool use_df64 = precision == WG_F64 && df64_fft_supported(pp.nu, pp.nv) &&
-                  (fft_impl == 2 || (fft_impl == 0 && epsilon >= 1e-11));
-  if (fft_impl == 2 && !use_df64)
-    return fail(set_error(WG_ERR_ARG, "double-float FFT needs WG_F64 and grid sides <= 6400"));
+  // plane FFTs: the kind the planner chose (FP64: pruned cuFFT Z2Z or the double-float FFT,
+  // whichever is cheaper with its rounding inside epsilon)
+  const bool use_df64 = pp.fft_kind == kFftDf64;
+  if (use_df64 && !df64_fft_supported(pp.nu, pp.nv))
+    return fail(set_error(WG_ERR_INTERNAL, "double-float FFT does not support %lld x %lld",
+                          (long long)pp.nu, (long long)pp.nv));
   // batch of planes: as many as the workspace budget allows
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return fail(set_error(WG_ERR_CUDA, "cudaMemGetInfo"));
@@ -458,7 +456,7 @@ int wg_plan_create(const double* uvw, const double* freq, int64_t nrows, int64_t
     while (B > 1 && workspace_layout(p.get(), B, 0).total > budget)
       B = std::max<int64_t>(1, align_batch(B * 3 / 4));
     p->batch = B;
-  } else if (precision == WG_F64 && (fft_impl == 3 || fft_impl == 0)) {
+  } else if (pp.fft_kind == kFftPrunedZ2Z) {
     // FP64 cuFFT is compute-bound on GB300: transform only the rows that hold the image
     // (degrid: rows are the first pass; grid: the last pass, on the rows the image needs)
     p->pruned = true;
@@ -521,6 +519,8 @@ int wg_plan_get_info(const wg_plan* p, wg_plan_info* info) {
   info->nvis = p->nvis; info->batch = p->batch;
   info->index_bytes = p->index_bytes; info->workspace_bytes = p->ws_bytes;
   info->umax = p->umax; info->vmax = p->vmax; info->wmin = p->wmin; info->wmax = p->wmax;
+  info->fft_impl = p->pp.fft_kind; info->rounding_gain = p->pp.gain;
+  info->err_model = p->pp.err_model;
   return WG_OK;
 }
 
@@ -570,7 +570,10 @@ enum { ST_PREP = 0, ST_SCREEN = 1, ST_FFT = 2, ST_GRID = 3, ST_ACCUM = 4, ST_OTH
 
 static int run_fft(wg_plan* p, int64_t nb, void* data, void* work, int dir, cudaStream_t s) {
   if (p->dfft != nullptr) {
-    cudaError_t e = df64_fft_exec(p->dfft, (double2*)data, nb, dir == CUFFT_FORWARD ? -1 : 1, s);
+    // the image occupies the first and last nx/2 rows of a plane: degrid's input is zero
+    // elsewhere and grid reads only those rows back
+    cudaError_t e = df64_fft_exec(p->dfft, (double2*)data, nb, dir == CUFFT_FORWARD ? -1 : 1, s,
+                                  p->g.nx);
     if (e != cudaSuccess) return set_error(WG_ERR_CUDA, "double-float FFT: %s", cudaGetErrorString(e));
     return WG_OK;
   }
@@ -889,6 +892,7 @@ int wg_plan_params(int64_t npix_x, int64_t npix_y, double pixsize_x, double pixs
   info->dw = pp.dw; info->w0 = pp.w0; info->nshift = pp.nshift; info->tile = pp.tile;
   info->ntiles = pp.ntu * pp.ntv; info->nvis = nvis;
   info->umax = umax; info->vmax = vmax; info->wmin = wmin; info->wmax = wmax;
+  info->fft_impl = pp.fft_kind; info->rounding_gain = pp.gain; info->err_model = pp.err_model;
   return WG_OK;
 }
 

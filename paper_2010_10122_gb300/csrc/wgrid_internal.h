@@ -72,7 +72,8 @@ struct Df64Fft;
 bool df64_fft_supported(int64_t nu, int64_t nv);
 cudaError_t df64_fft_create(int64_t nu, int64_t nv, Df64Fft** out);
 void df64_fft_destroy(Df64Fft* f);
-cudaError_t df64_fft_exec(Df64Fft* f, double2* data, int64_t batch, int sign, cudaStream_t s);
+cudaError_t df64_fft_exec(Df64Fft* f, double2* data, int64_t batch, int sign, cudaStream_t s,
+                          int64_t keep_rows = 0);
 
 // ---- index kernels (kernels_index.cu) ------------------------------------------------
 cudaError_t launch_extent(const double* uvw, int64_t nrows, unsigned long long* ext4,

@@ -61,7 +61,9 @@ class PlanInfo(ctypes.Structure):
                 ("tile", ctypes.c_int), ("ntiles", ctypes.c_int64), ("nvis", ctypes.c_int64),
                 ("batch", ctypes.c_int64), ("index_bytes", ctypes.c_size_t),
                 ("workspace_bytes", ctypes.c_size_t), ("umax", ctypes.c_double),
-                ("vmax", ctypes.c_double), ("wmin", ctypes.c_double), ("wmax", ctypes.c_double)]
+                ("vmax", ctypes.c_double), ("wmin", ctypes.c_double), ("wmax", ctypes.c_double),
+                ("fft_impl", ctypes.c_int), ("rounding_gain", ctypes.c_double),
+                ("err_model", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

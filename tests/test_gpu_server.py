@@ -1,6 +1,8 @@
 """Continuous batching on the GPU: mixed degrid / grid requests of several sizes, epsilons and
 precisions over resident observations run concurrently on stream slots; every result equals
 the same request run alone, within the parity tolerances; the memory budget bounds admission."""
+import math
+
 import numpy as np
 import pytest
 
@@ -58,17 +60,23 @@ def test_results_same_alone_and_in_the_mix(env):
     assert all(r.error is None for r in mixed)
     assert srv.max_inflight >= 2, "requests never overlapped"
     alone = make_requests(obs, Request)          # same seeds -> same data
-    run_serial(CudaExecutor(obs, slots=1), alone)
+    ex1 = CudaExecutor(obs, slots=1)
+    run_serial(ex1, alone)
     torch.cuda.synchronize()
     for a, b in zip(mixed, alone):
         x, y = a.result, b.result
         # relative L2 difference (the parity metric).  Degrid is order-independent, so bitwise
         # equal.  Grid sums footprints in an order that depends on the plan's bin-sort (the
         # order inside a bucket comes from atomics) and, in FP32, on shared-memory atomics; the
-        # two runs build separate plans, so they differ by rounding, bounded well below epsilon
+        # two runs build separate plans, so they differ by rounding: well below epsilon, and at
+        # most a few times the plan's plane-rounding term where that dominates (double-float
+        # planes: the rounding of two slightly different inputs is uncorrelated)
         err = ((x - y).abs().pow(2).sum() / y.abs().pow(2).sum()).sqrt().item()
-        tol = 0.1 * a.epsilon if a.direction == "grid" else 0.0
-        assert err <= tol, (a.obs, a.direction, a.precision, a.epsilon, err)
+        info = ex1.plans[(b.obs, b.epsilon, b.precision)].info
+        k_term = info["eps_kernel"] / 0.8
+        r_term = math.sqrt(max(info["err_model"] ** 2 - k_term ** 2, 0.0))
+        tol = max(0.1 * a.epsilon, 3 * r_term) if a.direction == "grid" else 0.0
+        assert err <= tol, (a.obs, a.direction, a.precision, a.epsilon, err, tol)
     rep = srv.report()
     assert rep["completed"] == len(mixed) and rep["p99_s"] >= rep["p50_s"]
 

@@ -1,7 +1,8 @@
 """Host-side checks of libwgrid.so that need no GPU: the C ABI exports, the built-in kernel
 table (App. A), the piecewise-polynomial kernel (Sec. 4.2), its Fourier transform psi, and
 the planner's definitions (Sec. 2: N = ceil(sigma n), Delta w, w_0, N_w; Sec. 4.1: smallest
-sigma per alpha that meets epsilon, cost-model choice across alpha)."""
+sigma per alpha that meets epsilon, cost-model choice across alpha), and the planner's model of
+plane rounding (the gain by which it reaches the result through the 1 / psi correction)."""
 import math
 import os
 import re
@@ -86,10 +87,18 @@ def _planner_case(wg, **kw):
 def test_planner_follows_sec2_definitions(wg, w_shift, prec, eps):
     a, info = _planner_case(wg, precision=prec, epsilon=eps, w_shift=w_shift)
     alpha, sigma = info["alpha"], info["sigma"]
-    # chosen kernel meets epsilon and is the smallest such sigma for its alpha (Sec. 4.1)
+    # chosen kernel meets epsilon and is the smallest such sigma for its alpha (Sec. 4.1), the
+    # error counting the kernel term and the plane rounding of the chosen FFT kind
     safety = 0.8   # default: table epsilon <= 0.8 x requested
     rows = [r for r in wg.kernel_table() if r[0] == alpha and r[2] <= safety * eps]
-    assert info["eps_kernel"] <= safety * eps and sigma == min(r[1] for r in rows)
+    assert info["eps_kernel"] <= safety * eps and info["err_model"] <= eps
+    for r in rows:
+        if r[1] < sigma:
+            alt = wg.plan_params(**a, force_alpha=alpha, force_sigma=r[1],
+                                 fft_impl=info["fft_impl"])
+            assert alt["err_model"] > eps
+    assert info["fft_impl"] == 1 if prec == "f32" else info["fft_impl"] in (2, 3)
+    assert info["err_model"] >= info["eps_kernel"] / safety
     # N >= ceil(sigma n), an FFT-friendly (11-smooth) multiple of the tile, and not much above
     for n, N in ((a["npix_x"], info["nu"]), (a["npix_y"], info["nv"])):
         assert N >= math.ceil(sigma * n) and N % info["tile"] == 0
@@ -116,11 +125,75 @@ def test_planner_without_wstacking_has_one_plane(wg):
 
 
 def test_planner_cost_prefers_cheap_fp32_kernels(wg):
-    """Sec. 4.1: across alpha the predicted cheapest kernel wins; FP64 at 1e-12 needs alpha 16."""
-    _, f64 = _planner_case(wg, precision="f64", epsilon=1e-12)
-    assert f64["alpha"] == 16 and f64["sigma"] == 1.55
+    """Sec. 4.1: across alpha the predicted cheapest kernel wins; FP64 at 1e-12 needs alpha 16
+    (sigma 1.55 with FP64 planes; the double-float FFT's larger rounding needs more)."""
+    _, f64 = _planner_case(wg, precision="f64", epsilon=1e-12, fft_impl=3)
+    assert f64["alpha"] == 16 and f64["sigma"] == 1.55 and f64["fft_impl"] == 3
+    _, df = _planner_case(wg, precision="f64", epsilon=1e-12, fft_impl=2)
+    assert df["alpha"] == 16 and df["sigma"] > 1.55 and df["fft_impl"] == 2
+    _, auto = _planner_case(wg, precision="f64", epsilon=1e-12)
+    assert auto["alpha"] == 16 and auto["fft_impl"] in (2, 3) and auto["err_model"] <= 1e-12
     _, f32 = _planner_case(wg)
-    assert f32["alpha"] in (7, 8, 12)
+    assert f32["alpha"] in (7, 8, 12) and f32["fft_impl"] == 1
+
+
+def _gain_reference(nx, ny, psx, psy, nu, nv, alpha, beta, mu, nshift, dw):
+    """rms of 1 / (n psi_u psi_v psi_w) over a 64 x 64 midpoint lattice of pixels, times
+    (int phi^2)^(3/2): the factor by which a relative rounding of the plane values reaches
+    degridded visibilities of an image with uniformly spread flux (unnormalised FFT: the rms
+    per cell of FFT(I corr) is ||I corr||; the footprint sums phi-weighted cells per axis).
+    Written with the oracle's phi and psi (the exponential of a semicircle itself)."""
+    x = np.linspace(-alpha / 2, alpha / 2, 40001)
+    phi2 = np.trapezoid(km.phi(x, alpha, beta, mu) ** 2, x)
+    jx = -nx / 2 + (np.arange(64) + 0.5) * nx / 64
+    jy = -ny / 2 + (np.arange(64) + 0.5) * ny / 64
+    L, M = np.meshgrid(jx * psx, jy * psy, indexing="ij")
+    r2 = L * L + M * M
+    n = np.sqrt(1 - r2)
+    nm1 = -r2 / (1 + n)
+    pu = km.psi(jx / nu, alpha, beta, mu)
+    pv = km.psi(jy / nv, alpha, beta, mu)
+    pw = km.psi(((nm1 - nshift) * dw).ravel(), alpha, beta, mu).reshape(nm1.shape)
+    corr = 1 / (n * pu[:, None] * pv[None, :] * pw)
+    return math.sqrt(np.mean(corr ** 2)) * phi2 ** 1.5
+
+
+@pytest.mark.parametrize("prec,eps,impl", [("f64", 1e-12, 2), ("f64", 1e-10, 3), ("f32", 1e-5, 0),
+                                           ("f32", 1e-3, 0)])
+def test_rounding_gain_matches_its_definition(wg, prec, eps, impl):
+    a, info = _planner_case(wg, precision=prec, epsilon=eps, fft_impl=impl)
+    ref = _gain_reference(a["npix_x"], a["npix_y"], a["pixsize_x"], a["pixsize_y"], info["nu"],
+                          info["nv"], info["alpha"], info["beta"], info["mu"], info["nshift"],
+                          info["dw"])
+    assert info["rounding_gain"] == pytest.approx(ref, rel=2e-3)
+    # the planner's rounding term: c u log2(nu nv) G, u the unit roundoff of the plane arithmetic
+    u = {1: 2.0 ** -24 if prec == "f32" else 2.0 ** -53, 2: 2.0 ** -47, 3: 2.0 ** -53}[info["fft_impl"]]
+    r = 0.06 * u * math.log2(info["nu"] * info["nv"]) * info["rounding_gain"]
+    k = info["eps_kernel"] / 0.8
+    assert info["err_model"] == pytest.approx(math.hypot(k, r), rel=1e-12)
+
+
+def test_rounding_gain_grows_as_sigma_shrinks(wg):
+    """1 / psi at the image edge grows as the oversampling drops (Sec. 3: the kernel's Fourier
+    transform decays towards |k| = 1 / (2 sigma))."""
+    gains = [wg.plan_params(**_planner_case(wg)[0] | dict(precision="f64", epsilon=1e-6,
+                                                          force_alpha=16, force_sigma=s))["rounding_gain"]
+             for s in (1.3, 1.5, 1.7, 2.0)]
+    assert all(g1 > g2 for g1, g2 in zip(gains, gains[1:]))
+
+
+def test_planner_fft_kind_arguments(wg):
+    with pytest.raises(wg.WgridError):
+        _planner_case(wg, precision="f32", fft_impl=2)
+    with pytest.raises(wg.WgridError):
+        _planner_case(wg, precision="f32", fft_impl=3)
+    with pytest.raises(wg.WgridError):
+        _planner_case(wg, precision="f64", epsilon=1e-9, fft_impl=4)
+    # grid sides beyond the double-float FFT's 6400
+    with pytest.raises(wg.WgridError) as ei:
+        _planner_case(wg, precision="f64", epsilon=1e-9, fft_impl=2, npix_x=8192, npix_y=8192,
+                      pixsize_x=math.radians(4 / 3600), pixsize_y=math.radians(4 / 3600))
+    assert "6400" in str(ei.value)
 
 
 @pytest.mark.parametrize("bad", [dict(npix_x=31), dict(npix_x=30), dict(npix_y=33),
