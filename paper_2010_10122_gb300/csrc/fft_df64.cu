@@ -63,10 +63,28 @@ __device__ __forceinline__ dd dd_mul(dd a, dd b) {
 
 __device__ __forceinline__ cdd c_add(cdd a, cdd b) { cdd c; c.r = dd_add(a.r, b.r); c.i = dd_add(a.i, b.i); return c; }
 __device__ __forceinline__ cdd c_sub(cdd a, cdd b) { cdd c; c.r = dd_sub(a.r, b.r); c.i = dd_sub(a.i, b.i); return c; }
+// x.h y.h + u.h v.h (sign: su = +1 or -1 for the second product) with the cross terms, as one
+// normalised pair: both leading products are split exactly (fma), summed exactly (two-sum),
+// and the small terms (product errors, cross products, low parts) are accumulated in float.
+// 19 FP32 operations instead of two products and a sum (25).
+__device__ __forceinline__ dd dd_dot2(dd x, dd y, dd u, dd v, float su) {
+  const float p1 = __fmul_rn(x.h, y.h);
+  const float e1 = __fmaf_rn(x.h, y.h, -p1);
+  const float uh = su * u.h, ul = su * u.l;
+  const float p2 = __fmul_rn(uh, v.h);
+  const float e2 = __fmaf_rn(uh, v.h, -p2);
+  dd s = two_sum(p1, p2);
+  float t = __fadd_rn(__fadd_rn(e1, e2), s.l);
+  t = __fmaf_rn(x.h, y.l, t);
+  t = __fmaf_rn(x.l, y.h, t);
+  t = __fmaf_rn(uh, v.l, t);
+  t = __fmaf_rn(ul, v.h, t);
+  return fast_two_sum(s.h, t);
+}
 __device__ __forceinline__ cdd c_mul(cdd a, cdd b) {
   cdd c;
-  c.r = dd_sub(dd_mul(a.r, b.r), dd_mul(a.i, b.i));
-  c.i = dd_add(dd_mul(a.r, b.i), dd_mul(a.i, b.r));
+  c.r = dd_dot2(a.r, b.r, a.i, b.i, -1.0f);
+  c.i = dd_dot2(a.r, b.i, a.i, b.r, 1.0f);
   return c;
 }
 __device__ __forceinline__ cdd c_scale(cdd a, dd s) { cdd c; c.r = dd_mul(a.r, s); c.i = dd_mul(a.i, s); return c; }
@@ -201,18 +219,25 @@ __device__ __forceinline__ void butterfly(cdd* x, bool fwd, const FftLine& L) {
   else dft_generic<R>(x, fwd, L.tw, L.n);
 }
 
+constexpr int kLoadBatch = 4;   // line elements a thread loads at once
+
 // One radix-R Stockham stage of a length-n line: butterfly j (j = tid, tid + T, ...) reads
 // src[j + kk M], twiddles, transforms and writes dst[(j / Ns) Ns R + j mod Ns + q Ns].
+// Shared-memory position of line element e: the low three bits of e are XORed with the next
+// three (swz = 7, lines whose length is a multiple of 8), so that the stride-R writes of the
+// first stages spread over the banks; a permutation within aligned groups of 8 elements.
+__device__ __forceinline__ int swizzle(int e, int swz) { return e ^ ((e >> 3) & swz); }
+
 template <int R>
 __device__ __forceinline__ void stage(const float4* __restrict__ src, float4* __restrict__ dst,
-                                      int n, int Ns, bool fwd, const FftLine& L) {
+                                      int n, int Ns, bool fwd, const FftLine& L, int swz) {
   const int M = n / R;
   const int tstep = n / (Ns * R);
   for (int j = threadIdx.x; j < M; j += blockDim.x) {
     const int jq = j / Ns, jm = j - jq * Ns;
     cdd x[R];
 #pragma unroll
-    for (int kk = 0; kk < R; ++kk) x[kk] = load_cdd(src[j + kk * M]);
+    for (int kk = 0; kk < R; ++kk) x[kk] = load_cdd(src[swizzle(j + kk * M, swz)]);
     if (Ns > 1) {
       // jm * kk * tstep < Ns * R * tstep = n: no reduction needed
 #pragma unroll
@@ -221,7 +246,7 @@ __device__ __forceinline__ void stage(const float4* __restrict__ src, float4* __
     butterfly<R>(x, fwd, L);
     const int idx = jq * Ns * R + jm;
 #pragma unroll
-    for (int q = 0; q < R; ++q) dst[idx + q * Ns] = store_cdd(x[q]);
+    for (int q = 0; q < R; ++q) dst[swizzle(idx + q * Ns, swz)] = store_cdd(x[q]);
   }
 }
 
@@ -240,22 +265,36 @@ k_fft_lines(const __grid_constant__ FftLine L, void* __restrict__ data, int64_t 
   extern __shared__ __align__(16) float4 fsm[];
   const int n = L.n;
   const int T = blockDim.x;
+  const int swz = (n & 7) == 0 ? 7 : 0;
   float4* src = fsm;
   float4* dst = fsm + n;
   const int plane = blockIdx.x / lines_per_plane;
   int line = blockIdx.x - plane * lines_per_plane;
   if (line >= split) line += skip;
   const int64_t base = (int64_t)plane * plane_elems + (int64_t)line * line_stride;
-  if (mode == 0) {
-    const double2* in = reinterpret_cast<const double2*>(data) + base;
-    for (int i = threadIdx.x; i < n; i += T) {
-      double2 v = in[i * elem_stride];
-      cdd x; x.r = split_double(v.x); x.i = split_double(v.y);
-      src[i] = store_cdd(x);
+  // load the line: kLoadBatch elements per thread in flight at once (a column is a strided
+  // gather)
+  for (int i0 = threadIdx.x; i0 < n; i0 += kLoadBatch * T) {
+    float4 v[kLoadBatch];
+#pragma unroll
+    for (int k = 0; k < kLoadBatch; ++k) {
+      const int i = i0 + k * T;
+      if (i < n) v[k] = reinterpret_cast<const float4*>(data)[base + i * elem_stride];
     }
-  } else {
-    const float4* in = reinterpret_cast<const float4*>(data) + base;
-    for (int i = threadIdx.x; i < n; i += T) src[i] = in[i * elem_stride];
+#pragma unroll
+    for (int k = 0; k < kLoadBatch; ++k) {
+      const int i = i0 + k * T;
+      if (i < n) {
+        if (mode == 0) {
+          double2 d = make_double2(__hiloint2double(__float_as_int(v[k].y), __float_as_int(v[k].x)),
+                                   __hiloint2double(__float_as_int(v[k].w), __float_as_int(v[k].z)));
+          cdd x; x.r = split_double(d.x); x.i = split_double(d.y);
+          src[swizzle(i, swz)] = store_cdd(x);
+        } else {
+          src[swizzle(i, swz)] = v[k];
+        }
+      }
+    }
   }
   __syncthreads();
   int Ns = 1;
@@ -263,15 +302,15 @@ k_fft_lines(const __grid_constant__ FftLine L, void* __restrict__ data, int64_t 
   for (int s = 0; s < L.nst; ++s) {
     const int R = L.radix[s];
     switch (R) {
-      case 3: stage<3>(src, dst, n, Ns, f, L); break;
-      case 4: stage<4>(src, dst, n, Ns, f, L); break;
-      case 5: stage<5>(src, dst, n, Ns, f, L); break;
-      case 8: stage<8>(src, dst, n, Ns, f, L); break;
+      case 3: stage<3>(src, dst, n, Ns, f, L, swz); break;
+      case 4: stage<4>(src, dst, n, Ns, f, L, swz); break;
+      case 5: stage<5>(src, dst, n, Ns, f, L, swz); break;
+      case 8: stage<8>(src, dst, n, Ns, f, L, swz); break;
       default:
         if (kAll) {
-          if (R == 2) stage<2>(src, dst, n, Ns, f, L);
-          else if (R == 7) stage<7>(src, dst, n, Ns, f, L);
-          else stage<11>(src, dst, n, Ns, f, L);
+          if (R == 2) stage<2>(src, dst, n, Ns, f, L, swz);
+          else if (R == 7) stage<7>(src, dst, n, Ns, f, L, swz);
+          else stage<11>(src, dst, n, Ns, f, L, swz);
         }
         break;
     }
@@ -281,11 +320,11 @@ k_fft_lines(const __grid_constant__ FftLine L, void* __restrict__ data, int64_t 
   }
   if (mode == 0) {
     float4* out = reinterpret_cast<float4*>(data) + base;
-    for (int i = threadIdx.x; i < n; i += T) out[i * elem_stride] = src[i];
+    for (int i = threadIdx.x; i < n; i += T) out[i * elem_stride] = src[swizzle(i, swz)];
   } else {
     double2* out = reinterpret_cast<double2*>(data) + base;
     for (int i = threadIdx.x; i < n; i += T) {
-      cdd x = load_cdd(src[i]);
+      cdd x = load_cdd(src[swizzle(i, swz)]);
       double2 v; v.x = join_double(x.r); v.y = join_double(x.i);
       out[i * elem_stride] = v;
     }
