@@ -214,6 +214,51 @@ def algorithmic_flops_per_vis(alpha):
     return 4 * alpha ** 3 + 3 * alpha * 2 * (alpha + 3)
 
 
+# FP32 arithmetic instructions of the double-float FFT (paper_2010_10122_gb300/csrc/fft_df64.cu),
+# counted from its operations: double-float add 11 (two-sum 6, two adds, renormalisation 3),
+# product 7, complex add 22, scale by a constant 14, twiddle product 38 (two fused two-product
+# sums of 19); butterflies: radix 2 44, 3 160, 4 176, 5 464, 8 600, generic R (7, 11) R(R-1) x 60.
+DF64_BUTTERFLY = {2: 44, 3: 160, 4: 176, 5: 464, 8: 600}
+
+
+def df64_radices(n):
+    """Radix plan of a double-float line transform (8s and 4s for the power of two, a single 2
+    only for n = 2 x odd, then 5, 3, 7, 11) -- the plan the library uses."""
+    m, p2 = n, 0
+    while m % 2 == 0:
+        m //= 2
+        p2 += 1
+    r = []
+    if p2 == 1:
+        r.append(2)
+    else:
+        e8, rem = p2 // 3, p2 % 3
+        if rem == 1:
+            e8 -= 1
+        r += [8] * e8 + ([4, 4] if rem == 1 else [4] if rem == 2 else [])
+    for p in (5, 3, 7, 11):
+        while m % p == 0:
+            r.append(p)
+            m //= p
+    return r
+
+
+def df64_line_ops(n):
+    """FP32 instructions of one length-n double-float line transform (butterflies and the
+    twiddle products of every stage after the first)."""
+    ops, ns = 0, 1
+    for r in df64_radices(n):
+        bf = DF64_BUTTERFLY.get(r, r * (r - 1) * 60)
+        ops += (n // r) * (bf + (38 * (r - 1) if ns > 1 else 0))
+        ns *= r
+    return ops
+
+
+# DRAM bytes the double-float FFT moves per plane cell and pass, measured by ncu on 3456^2
+# planes (row pass 30.7, column pass 30.9: profiles/k_fft_lines_df64_3456.md)
+DF64_DRAM_BYTES_PER_CELL_PASS = 30.8
+
+
 def run_sweep(args):
     """Precision sweep (eps in {1e-3, 1e-5 FP32; 1e-7, 1e-10, 1e-12 FP64}): per epsilon the
     degrid and grid vis/s (CUDA events, resident plan) and the relative L2 error against the
@@ -471,11 +516,28 @@ def main():
             stage_ms[(prec, direction, "gridding")] = s["ms_grid"]
             stage_ms[(prec, direction, "screen" if direction == "degrid" else "accumulate")] = (
                 s["ms_screen"] if direction == "degrid" else s["ms_accum"])
+            if plans[prec].info["fft_impl"] == 2:   # the library's own FFT kernel
+                stage_ms[(prec, direction, "fft")] = s["ms_fft"]
     dom = max(stage_ms, key=stage_ms.get)
     prec_d, dir_d, stage_d = dom
     info_d = plans[prec_d].info
     roof = None
-    if stage_d == "gridding" and prec_d == "f64":
+    if stage_d == "fft":
+        # double-float plane FFT: FP32-ALU (issue) bound; work = its FP32 arithmetic
+        # instructions; one pass over the nx image rows (length nv), one over all nv columns
+        nu, nv, nw = info_d["nu"], info_d["nv"], info_d["nw"]
+        ops = nw * (obs.npix_x * df64_line_ops(nv) + nv * df64_line_ops(nu))
+        peak = 152 * 128 * 2.07e9   # SMs x FP32 lanes x max SM clock, one instruction per lane
+        ach = ops / (stage_ms[dom] * 1e-3)
+        cells_passes = nw * (obs.npix_x * nv + nv * nu)
+        roof = {"bound": "alu", "kernel": "k_fft_lines (double-float plane FFT, row + column pass)",
+                "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": DF64_DRAM_BYTES_PER_CELL_PASS * cells_passes,
+                "algorithmic_bytes": 32 * cells_passes,
+                "peak_source": "FP32 arithmetic instructions/s: 152 SMs x 128 lanes x 2.07 GHz "
+                               "(an FMA counts once)",
+                "stage": f"{prec_d} {dir_d}"}
+    elif stage_d == "gridding" and prec_d == "f64":
         flops = algorithmic_flops_per_vis(info_d["alpha"]) * plans[prec_d].info["nvis"]
         peak = 1.25e12   # FP64 FMA pipe: nominal GB300 rate (152 SMs x 2 FMA/clk x 2 x 2.07 GHz)
         ach = flops / (stage_ms[dom] * 1e-3)

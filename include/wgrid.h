@@ -104,8 +104,9 @@ typedef struct wg_stats {
   int64_t n_batches;   /* plane batches processed */
   int64_t n_planes;    /* w-planes processed */
   size_t workspace_bytes; /* device workspace used by the call */
-  int64_t n_kernels;   /* library kernels launched by the call (cuFFT's own not counted) */
-  int64_t n_fft_calls; /* cuFFT executions */
+  int64_t n_kernels;   /* library kernels launched by the call, the double-float FFT's passes
+                          included (cuFFT's own not counted) */
+  int64_t n_fft_calls; /* plane-FFT executions (one per batch of planes) */
 } wg_stats;
 
 /* Plan parameters chosen by the planner (Sec. 4.1, App. A). */

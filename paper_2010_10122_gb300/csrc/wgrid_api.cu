@@ -670,7 +670,8 @@ static int degrid_impl(wg_plan* p, const R* dirty, const R* wgt, typename C2<R>:
     std::memset(stats, 0, sizeof(*stats));
     tm.finish(stats);
     stats->n_batches = nbatches; stats->n_planes = g.nw; stats->workspace_bytes = w.total;
-    stats->n_kernels = 2 * nbatches + 1 + (wts != nullptr);   // screen + degrid per batch, finalize, weights
+    // screen + degrid per batch, finalize, weights; the double-float FFT's two passes per batch
+    stats->n_kernels = 2 * nbatches + 1 + (wts != nullptr) + (p->dfft != nullptr ? 2 * nbatches : 0);
     stats->n_fft_calls = nbatches;
   }
   return WG_OK;
@@ -728,7 +729,8 @@ static int grid_impl(wg_plan* p, const typename C2<R>::T* vis, const R* wgt, R* 
     std::memset(stats, 0, sizeof(*stats));
     tm.finish(stats);
     stats->n_batches = nbatches; stats->n_planes = g.nw; stats->workspace_bytes = w.total;
-    stats->n_kernels = 2 * nbatches + (wts != nullptr);   // grid + accumulate per batch, weights
+    // grid + accumulate per batch, weights; the double-float FFT's two passes per batch
+    stats->n_kernels = 2 * nbatches + (wts != nullptr) + (p->dfft != nullptr ? 2 * nbatches : 0);
     stats->n_fft_calls = nbatches;
   }
   return WG_OK;
