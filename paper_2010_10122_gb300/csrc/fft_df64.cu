@@ -254,14 +254,16 @@ __device__ __forceinline__ void stage(const float4* __restrict__ src, float4* __
 // plane * plane_elems + line * line_stride + i * elem_stride (complex elements).  The plane's
 // transformed lines are numbered 0 .. lines_per_plane - 1; those from `split` on are shifted
 // by `skip` (a pass over the first and last rows of a plane only, skipping the middle).
-// mode 0: load doubles, store df64; mode 1: load df64, store doubles.  Two n-element
+// mode 0: load doubles, store df64; mode 1: load df64, store doubles.  Elements lhalf ..
+// n - lhalf - 1 are known zeros and not loaded, elements shalf .. n - shalf - 1 are not stored
+// (lhalf = shalf = n: everything).  Two n-element
 // shared-memory buffers (ping-pong); kAll adds the rare radices 2, 7 and 11, kept out of the
 // common instance so that its register allocation is not burdened with them.
 template <int TMAX, int MINB, bool kAll>
 __global__ void __launch_bounds__(TMAX, MINB)
 k_fft_lines(const __grid_constant__ FftLine L, void* __restrict__ data, int64_t plane_elems,
             int lines_per_plane, int64_t line_stride, int64_t elem_stride, int mode, int fwd,
-            int split, int skip) {
+            int split, int skip, int lhalf, int shalf) {
   extern __shared__ __align__(16) float4 fsm[];
   const int n = L.n;
   const int T = blockDim.x;
@@ -279,7 +281,12 @@ k_fft_lines(const __grid_constant__ FftLine L, void* __restrict__ data, int64_t 
 #pragma unroll
     for (int k = 0; k < kLoadBatch; ++k) {
       const int i = i0 + k * T;
-      if (i < n) v[k] = reinterpret_cast<const float4*>(data)[base + i * elem_stride];
+      if (i < n) {
+        if (i < lhalf || i >= n - lhalf)
+          v[k] = reinterpret_cast<const float4*>(data)[base + i * elem_stride];
+        else
+          v[k] = make_float4(0.f, 0.f, 0.f, 0.f);   // known zero: not loaded
+      }
     }
 #pragma unroll
     for (int k = 0; k < kLoadBatch; ++k) {
@@ -320,10 +327,12 @@ k_fft_lines(const __grid_constant__ FftLine L, void* __restrict__ data, int64_t 
   }
   if (mode == 0) {
     float4* out = reinterpret_cast<float4*>(data) + base;
-    for (int i = threadIdx.x; i < n; i += T) out[i * elem_stride] = src[swizzle(i, swz)];
+    for (int i = threadIdx.x; i < n; i += T)
+      if (i < shalf || i >= n - shalf) out[i * elem_stride] = src[swizzle(i, swz)];
   } else {
     double2* out = reinterpret_cast<double2*>(data) + base;
     for (int i = threadIdx.x; i < n; i += T) {
+      if (i >= shalf && i < n - shalf) continue;   // not needed downstream
       cdd x = load_cdd(src[swizzle(i, swz)]);
       double2 v; v.x = join_double(x.r); v.y = join_double(x.i);
       out[i * elem_stride] = v;
@@ -414,7 +423,8 @@ void df64_fft_destroy(Df64Fft* f) {
 
 static cudaError_t launch_lines(const FftLine& L, double2* data, int64_t batch, int64_t plane,
                                 int lines_per_plane, int64_t line_stride, int64_t elem_stride,
-                                int mode, int fwd, int split, int skip, cudaStream_t s) {
+                                int mode, int fwd, int split, int skip, int lhalf, int shalf,
+                                cudaStream_t s) {
   if (lines_per_plane == 0 || batch == 0) return cudaSuccess;
   const size_t smem = 2 * sizeof(float4) * (size_t)L.n;
   const int64_t blocks = batch * lines_per_plane;
@@ -424,7 +434,8 @@ static cudaError_t launch_lines(const FftLine& L, double2* data, int64_t batch, 
     if (L.radix[i] == 2 || L.radix[i] == 7 || L.radix[i] == 11) common = false;
 #define WG_LINES(TM, MB, A)                                                                     \
   k_fft_lines<TM, MB, A><<<(unsigned)blocks, L.threads, smem, s>>>(                             \
-      L, data, plane, lines_per_plane, line_stride, elem_stride, mode, fwd, split, skip)
+      L, data, plane, lines_per_plane, line_stride, elem_stride, mode, fwd, split, skip, lhalf, \
+      shalf)
   if (L.threads <= 448) {
     if (common) WG_LINES(448, 2, false); else WG_LINES(448, 2, true);
   } else {
@@ -435,32 +446,37 @@ static cudaError_t launch_lines(const FftLine& L, double2* data, int64_t batch, 
 }
 
 // In-place transform of `batch` nu x nv complex128 planes; sign -1 forward, +1 inverse.
-// keep_rows = 0: the full 2-D transform.  keep_rows = k (even, < nu): only the first and last
-// k/2 rows of a plane matter -- forward: they hold the only nonzero input, so the row pass
-// runs over them alone (the other rows stay zero, whose bits are the same in both formats);
-// inverse: only they are read afterwards, so the column pass runs first and the row pass over
-// them alone, and the other rows are left in the intermediate (df64) format.
+// keep_rows = keep_cols = 0: the full 2-D transform.  Otherwise only the image block -- the first
+// and last keep_rows/2 rows and keep_cols/2 columns of a plane -- matters:
+//  forward: it holds the only nonzero input, so the row pass runs over the image rows and
+//    loads only their image columns, and the column pass loads only the image rows (the rest
+//    is zero and never read, so the caller need not write it);
+//  inverse: only it is read afterwards, so the column pass runs first and the row pass over the
+//    image rows, storing only their image columns (other cells are left undefined).
 cudaError_t df64_fft_exec(Df64Fft* f, double2* data, int64_t batch, int sign, cudaStream_t s,
-                          int64_t keep_rows) {
+                          int64_t keep_rows, int64_t keep_cols) {
   const int64_t plane = (int64_t)f->nu * f->nv;
   const int fwd = sign < 0 ? 1 : 0;
-  const bool prune = keep_rows > 0 && keep_rows < f->nu;
-  if (prune && (keep_rows & 1)) return cudaErrorInvalidValue;
-  const int half = prune ? (int)(keep_rows / 2) : f->nu;
-  const int skip = prune ? f->nu - (int)keep_rows : 0;
-  const int nrows = prune ? (int)keep_rows : f->nu;
+  const bool prune = keep_rows > 0 && keep_cols > 0;
+  if (prune && ((keep_rows & 1) || (keep_cols & 1) || keep_rows > f->nu || keep_cols > f->nv))
+    return cudaErrorInvalidValue;
+  const int rh = prune ? (int)(keep_rows / 2) : f->nu;   // image half-extent along u (rows)
+  const int ch = prune ? (int)(keep_cols / 2) : f->nv;   // along v (columns)
+  const int nrows = prune ? 2 * rh : f->nu;
+  const int skip = f->nu - nrows;
+  const int split = prune ? rh : f->nu;
   cudaError_t e;
   if (!prune || fwd) {
     // rows (length nv, contiguous): doubles -> df64; then columns (length nu, stride nv):
     // df64 -> doubles
-    e = launch_lines(f->lv, data, batch, plane, nrows, f->nv, 1, 0, fwd, half, skip, s);
+    e = launch_lines(f->lv, data, batch, plane, nrows, f->nv, 1, 0, fwd, split, skip, ch, f->nv, s);
     if (e != cudaSuccess) return e;
-    return launch_lines(f->lu, data, batch, plane, f->nv, 1, f->nv, 1, fwd, f->nv, 0, s);
+    return launch_lines(f->lu, data, batch, plane, f->nv, 1, f->nv, 1, fwd, f->nv, 0, rh, f->nu, s);
   }
-  // pruned inverse: columns doubles -> df64, then the kept rows df64 -> doubles
-  e = launch_lines(f->lu, data, batch, plane, f->nv, 1, f->nv, 0, fwd, f->nv, 0, s);
+  // pruned inverse: columns doubles -> df64, then the image rows df64 -> doubles
+  e = launch_lines(f->lu, data, batch, plane, f->nv, 1, f->nv, 0, fwd, f->nv, 0, f->nu, f->nu, s);
   if (e != cudaSuccess) return e;
-  return launch_lines(f->lv, data, batch, plane, nrows, f->nv, 1, 1, fwd, half, skip, s);
+  return launch_lines(f->lv, data, batch, plane, nrows, f->nv, 1, 1, fwd, split, skip, f->nv, ch, s);
 }
 
 }  // namespace wg

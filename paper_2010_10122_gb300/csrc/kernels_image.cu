@@ -87,32 +87,40 @@ __device__ __forceinline__ int cell_to_pixel(int x, int n, int N) {
   return -1;
 }
 
-// Screen values e^{2 pi i cycles(j)} for consecutive planes j = j0, j0 + 1, ...
-// FP32: each plane from its exactly reduced phase with sincospif.  FP64: sincospi at an anchor
-// plane every kAnchor planes and a complex rotation by e^{2 pi i B} in between (4 FMAs per
-// plane instead of an FP64 sincospi; the rotation's rounding grows by ~1e-16 per plane and is
-// reset at each anchor).
+// Screen values v e^{2 pi i cycles(j)} for consecutive planes j = j0, j0 + 1, ... (v = 1 for the
+// plain screen, the corrected pixel value for the screened image).  FP32: each plane from its
+// exactly reduced phase with sincospif.  FP64: sincospi at an anchor plane every kAnchor planes
+// and a complex rotation by e^{2 pi i B} in between (4 FMAs per plane instead of an FP64
+// sincospi; the rotation's rounding grows by ~1e-16 per plane and is reset at each anchor).
 constexpr int kAnchor = 16;
 template <typename R> struct ScreenIter;
 template <> struct ScreenIter<float> {
-  Z4<float> t; int j; float c, s;
-  __device__ void start(const Z4<float>& tt, int j0) { t = tt; j = j0; eval(); }
-  __device__ void eval() { float cyc = screen_cycles(t, j); sincos2pi(cyc, &s, &c); }
+  Z4<float> t; int j; float v, c, s;
+  __device__ void start(const Z4<float>& tt, int j0, float vv = 1.0f) { t = tt; j = j0; v = vv; eval(); }
+  __device__ void eval() {
+    float cyc = screen_cycles(t, j);
+    sincos2pi(cyc, &s, &c);
+    c *= v; s *= v;
+  }
   __device__ void next() { ++j; eval(); }
 };
 template <> struct ScreenIter<double> {
-  Z4<double> t; int j, k; double c, s, rc, rs;
-  __device__ void start(const Z4<double>& tt, int j0) {
-    t = tt; j = j0; k = 0;
+  Z4<double> t; int j, k; double v, c, s, rc, rs;
+  __device__ void start(const Z4<double>& tt, int j0, double vv = 1.0) {
+    t = tt; j = j0; k = 0; v = vv;
     double b = t.w - rint(t.w);
     sincos2pi(b, &rs, &rc);
+    anchor();
+  }
+  __device__ void anchor() {
     sincos2pi(screen_cycles(t, j), &s, &c);
+    c *= v; s *= v;
   }
   __device__ void next() {
     ++j;
     if (++k == kAnchor) {
       k = 0;
-      sincos2pi(screen_cycles(t, j), &s, &c);
+      anchor();
     } else {
       double nc = fma(c, rc, -s * rs);
       s = fma(s, rc, c * rs);
@@ -124,22 +132,35 @@ template <> struct ScreenIter<double> {
 // ---------------------------------------------------------------------------------------
 // screen: planes[p] = I * corr * exp(+2 pi i c_j (n - 1 - nshift)) at the image cells, 0
 // elsewhere (Eqs. R1, R2 with the sign of Eq. rime), for global planes j = b0 .. b0 + nb - 1.
+// image_only: one thread per image pixel, the padding cells are not written (the plane FFT
+// treats them as zeros without reading them); otherwise one thread per plane cell.
 // ---------------------------------------------------------------------------------------
 template <typename R>
 __global__ void k_screen(const Geom g, const R* __restrict__ dirty,
                          const Z4<R>* __restrict__ table, typename C2<R>::T* __restrict__ planes,
-                         int b0, int nb) {
+                         int b0, int nb, int image_only) {
   using CT = typename C2<R>::T;
-  int y = blockIdx.x * blockDim.x + threadIdx.x;
-  int x = blockIdx.y;
-  if (y >= g.nv) return;
   const int64_t ncell = (int64_t)g.nu * g.nv;
-  const int64_t cell = (int64_t)x * g.nv + y;
-  int jx = cell_to_pixel(x, g.nx, g.nu), jy = cell_to_pixel(y, g.ny, g.nv);
-  if (jx < 0 || jy < 0) {
-    CT zero; zero.x = (R)0; zero.y = (R)0;
-    for (int p = 0; p < nb; ++p) planes[p * ncell + cell] = zero;
-    return;
+  int jx, jy;
+  int64_t cell;
+  if (image_only) {
+    jy = blockIdx.x * blockDim.x + threadIdx.x;
+    jx = blockIdx.y;
+    if (jy >= g.ny) return;
+    const int x = jx < g.nx / 2 ? g.nu - g.nx / 2 + jx : jx - g.nx / 2;
+    const int y = jy < g.ny / 2 ? g.nv - g.ny / 2 + jy : jy - g.ny / 2;
+    cell = (int64_t)x * g.nv + y;
+  } else {
+    const int y = blockIdx.x * blockDim.x + threadIdx.x;
+    const int x = blockIdx.y;
+    if (y >= g.nv) return;
+    cell = (int64_t)x * g.nv + y;
+    jx = cell_to_pixel(x, g.nx, g.nu); jy = cell_to_pixel(y, g.ny, g.nv);
+    if (jx < 0 || jy < 0) {
+      CT zero; zero.x = (R)0; zero.y = (R)0;
+      for (int p = 0; p < nb; ++p) planes[p * ncell + cell] = zero;
+      return;
+    }
   }
   const int64_t pix = (int64_t)jx * g.ny + jy;
   const Z4<R> t = table[pix];
@@ -150,9 +171,9 @@ __global__ void k_screen(const Geom g, const R* __restrict__ dirty,
     return;
   }
   ScreenIter<R> it;
-  it.start(t, b0);
+  it.start(t, b0, val);
   for (int p = 0; p < nb; ++p) {
-    CT v; v.x = val * it.c; v.y = val * it.s;
+    CT v; v.x = it.c; v.y = it.s;
     planes[p * ncell + cell] = v;
     it.next();
   }
@@ -160,9 +181,15 @@ __global__ void k_screen(const Geom g, const R* __restrict__ dirty,
 
 template <typename R>
 cudaError_t launch_screen(const Geom& g, const R* dirty, const Z4<R>* table,
-                          typename C2<R>::T* planes, int b0, int nb, cudaStream_t s) {
-  dim3 grid((g.nv + 255) / 256, g.nu);
-  k_screen<R><<<grid, 256, 0, s>>>(g, dirty, table, planes, b0, nb);
+                          typename C2<R>::T* planes, int b0, int nb, bool image_only,
+                          cudaStream_t s) {
+  if (image_only) {
+    dim3 grid((g.ny + 255) / 256, g.nx);
+    k_screen<R><<<grid, 256, 0, s>>>(g, dirty, table, planes, b0, nb, 1);
+  } else {
+    dim3 grid((g.nv + 255) / 256, g.nu);
+    k_screen<R><<<grid, 256, 0, s>>>(g, dirty, table, planes, b0, nb, 0);
+  }
   return cudaGetLastError();
 }
 
@@ -215,7 +242,7 @@ cudaError_t launch_accumulate(const Geom& g, const Z4<R>* table, const typename 
 #define WG_INST(R)                                                                          \
   template cudaError_t launch_prep<R>(const ImgParams&, Z4<R>*, cudaStream_t);              \
   template cudaError_t launch_screen<R>(const Geom&, const R*, const Z4<R>*, C2<R>::T*, int, \
-                                        int, cudaStream_t);                                 \
+                                        int, bool, cudaStream_t);                           \
   template cudaError_t launch_accumulate<R>(const Geom&, const Z4<R>*, const C2<R>::T*, int, \
                                             int, double*, bool, bool, R*, cudaStream_t);
 WG_INST(float)

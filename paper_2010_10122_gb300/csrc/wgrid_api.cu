@@ -570,10 +570,10 @@ enum { ST_PREP = 0, ST_SCREEN = 1, ST_FFT = 2, ST_GRID = 3, ST_ACCUM = 4, ST_OTH
 
 static int run_fft(wg_plan* p, int64_t nb, void* data, void* work, int dir, cudaStream_t s) {
   if (p->dfft != nullptr) {
-    // the image occupies the first and last nx/2 rows of a plane: degrid's input is zero
-    // elsewhere and grid reads only those rows back
+    // the image occupies the first and last nx/2 rows and ny/2 columns of a plane: degrid's
+    // input is zero elsewhere (and not written by the screen) and grid reads only that block
     cudaError_t e = df64_fft_exec(p->dfft, (double2*)data, nb, dir == CUFFT_FORWARD ? -1 : 1, s,
-                                  p->g.nx);
+                                  p->g.nx, p->g.ny);
     if (e != cudaSuccess) return set_error(WG_ERR_CUDA, "double-float FFT: %s", cudaGetErrorString(e));
     return WG_OK;
   }
@@ -648,7 +648,8 @@ static int degrid_impl(wg_plan* p, const R* dirty, const R* wgt, typename C2<R>:
     }
     for (int64_t b0 = 0; b0 < g.nw; b0 += p->batch) {
       int nb = (int)std::min<int64_t>(p->batch, g.nw - b0);
-      e = launch_screen<R>(g, dirty, table, planes, (int)b0, nb, s);
+      // with the double-float FFT the screen writes only the image cells (see df64_fft_exec)
+      e = launch_screen<R>(g, dirty, table, planes, (int)b0, nb, p->dfft != nullptr, s);
       if (e != cudaSuccess) { rc = set_error(WG_ERR_CUDA, "screen: %s", cudaGetErrorString(e)); break; }
       tm.mark(ST_SCREEN);
       if ((rc = run_fft(p, nb, planes, fftw, CUFFT_FORWARD, s)) != WG_OK) break;

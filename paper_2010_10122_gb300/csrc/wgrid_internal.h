@@ -73,7 +73,7 @@ bool df64_fft_supported(int64_t nu, int64_t nv);
 cudaError_t df64_fft_create(int64_t nu, int64_t nv, Df64Fft** out);
 void df64_fft_destroy(Df64Fft* f);
 cudaError_t df64_fft_exec(Df64Fft* f, double2* data, int64_t batch, int sign, cudaStream_t s,
-                          int64_t keep_rows = 0);
+                          int64_t keep_rows = 0, int64_t keep_cols = 0);
 
 // ---- index kernels (kernels_index.cu) ------------------------------------------------
 cudaError_t launch_extent(const double* uvw, int64_t nrows, unsigned long long* ext4,
@@ -95,7 +95,8 @@ template <typename R>
 cudaError_t launch_prep(const ImgParams& P, Z4<R>* table, cudaStream_t s);
 template <typename R>
 cudaError_t launch_screen(const Geom& g, const R* dirty, const Z4<R>* table,
-                          typename C2<R>::T* planes, int b0, int nb, cudaStream_t s);
+                          typename C2<R>::T* planes, int b0, int nb, bool image_only,
+                          cudaStream_t s);
 template <typename R>
 cudaError_t launch_accumulate(const Geom& g, const Z4<R>* table,
                               const typename C2<R>::T* planes, int b0, int nb, double* acc,
