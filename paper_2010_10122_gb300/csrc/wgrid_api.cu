@@ -130,6 +130,7 @@ struct wg_plan {
   bool has_row = false, has_col = false;
   int degrid_bs = 1;         // planes per degrid CTA; batches are multiples of it
   bool use_wts = false;      // per-call kernel-value table (FP64, when it fits the workspace)
+  void* wts_plan = nullptr;  // plan-resident kernel-value table (FP64, when it is small)
   int nslot = 1;             // degrid partial-sum slots per visibility
   size_t fft_ws = 0;
   size_t ws_bytes = 0;
@@ -148,7 +149,8 @@ void wg_default_options(wg_options* opt) {
 }
 
 static int free_plan_device(wg_plan* p) {
-  void* ptrs[] = {p->chan4, p->cinv_u, p->cinv_v, p->off, p->idx, p->meta, p->z, p->ph, p->table};
+  void* ptrs[] = {p->chan4, p->cinv_u, p->cinv_v, p->off, p->idx, p->meta, p->z, p->ph, p->table,
+                  p->wts_plan};
   for (void* q : ptrs)
     if (q != nullptr) cudaFree(q);
   if (p->has_full) cufftDestroy(p->fft_full);
@@ -444,10 +446,14 @@ int wg_plan_create(const double* uvw, const double* freq, int64_t nrows, int64_t
   };
   if (B < pp.nw) B = align_batch(B);
   if (B < p->degrid_bs && B < pp.nw) p->degrid_bs = (int)B;   // tiny budgets: one sub-batch per batch
-  // FP64: evaluate each visibility's kernel values once per call (the FP64 pipe is the limit
-  // of the (de)gridding kernels, and Horner on every tile / sub-batch visit doubles its work)
-  p->use_wts = precision == WG_F64 &&
-               (size_t)p->nvis * 3 * kMaxG * 8 <= budget / 4;
+  // FP64: the (de)gridding kernels are bound by the FP64 pipe, and Horner on every tile /
+  // sub-batch visit doubles their work, so each visibility's kernel values are evaluated once:
+  // with the plan when the table is small (they depend only on the plan's coordinates), else
+  // once per call when it fits a quarter of the workspace
+  const size_t wts_bytes = (size_t)std::max<int64_t>(1, p->nvis) * 3 * kMaxG * 8;
+  const bool wts_resident = precision == WG_F64 && p->nvis > 0 &&
+                            wts_bytes <= std::min<size_t>((size_t)4 << 30, free_b / 16);
+  p->use_wts = precision == WG_F64 && !wts_resident && wts_bytes <= budget / 4;
   p->nslot = (g.alpha_w - 1 + p->degrid_bs - 1) / p->degrid_bs + 1;
   if (use_df64) {
     cudaError_t e = df64_fft_create(pp.nu, pp.nv, &p->dfft);
@@ -490,6 +496,15 @@ int wg_plan_create(const double* uvw, const double* freq, int64_t nrows, int64_t
       p->has_rem = true;
       p->fft_ws = std::max(p->fft_ws, ws);
     }
+  }
+  if (wts_resident) {
+    if ((rc = dev_alloc((unsigned char**)&p->wts_plan, wts_bytes)) != WG_OK) return fail(rc);
+    IndexView<double> ixd{p->off, p->idx, p->meta, (const Z4<double>*)p->z,
+                          (const double2*)p->ph, nullptr};
+    cudaError_t e = launch_weights<double>(g, p->coef_d, ixd, p->nvis, (double*)p->wts_plan, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(set_error(WG_ERR_CUDA, "kernel values: %s", cudaGetErrorString(e)));
+    p->index_bytes += wts_bytes;
   }
   p->ws_bytes = workspace_layout(p.get(), B, p->fft_ws).total;
   if (p->opt.max_workspace != 0 && p->ws_bytes > p->opt.max_workspace)
@@ -633,7 +648,8 @@ static int degrid_impl(wg_plan* p, const R* dirty, const R* wgt, typename C2<R>:
   auto* planes = (typename C2<R>::T*)ws;
   void* fftw = ws + w.planes;
   auto* partial = (typename C2<R>::T*)(ws + w.planes + w.fft);
-  R* wts = w.wts ? (R*)(ws + w.planes + w.fft + w.acc) : nullptr;
+  R* wts_call = w.wts ? (R*)(ws + w.planes + w.fft + w.acc) : nullptr;   // filled per call
+  R* wts = p->wts_plan ? (R*)p->wts_plan : wts_call;
   const auto* table = (const Z4<R>*)p->table;
   int rc = WG_OK;
   IndexView<R> ix{p->off, p->idx, p->meta, (const Z4<R>*)p->z, (const typename C2<R>::T*)p->ph, wts};
@@ -642,8 +658,8 @@ static int degrid_impl(wg_plan* p, const R* dirty, const R* wgt, typename C2<R>:
   int64_t nbatches = 0;
   do {
     cudaError_t e = cudaSuccess;
-    if (wts != nullptr) {
-      e = launch_weights<R>(g, coef, ix, p->nvis, wts, s);
+    if (wts_call != nullptr) {
+      e = launch_weights<R>(g, coef, ix, p->nvis, wts_call, s);
       if (e != cudaSuccess) { rc = set_error(WG_ERR_CUDA, "weights: %s", cudaGetErrorString(e)); break; }
     }
     for (int64_t b0 = 0; b0 < g.nw; b0 += p->batch) {
@@ -672,7 +688,7 @@ static int degrid_impl(wg_plan* p, const R* dirty, const R* wgt, typename C2<R>:
     tm.finish(stats);
     stats->n_batches = nbatches; stats->n_planes = g.nw; stats->workspace_bytes = w.total;
     // screen + degrid per batch, finalize, weights; the double-float FFT's two passes per batch
-    stats->n_kernels = 2 * nbatches + 1 + (wts != nullptr) + (p->dfft != nullptr ? 2 * nbatches : 0);
+    stats->n_kernels = 2 * nbatches + 1 + (wts_call != nullptr) + (p->dfft != nullptr ? 2 * nbatches : 0);
     stats->n_fft_calls = nbatches;
   }
   return WG_OK;
@@ -697,7 +713,8 @@ static int grid_impl(wg_plan* p, const typename C2<R>::T* vis, const R* wgt, R* 
   void* fftw = ws + w.planes;
   const auto* table = (const Z4<R>*)p->table;
   auto* acc = (double*)(ws + w.planes + w.fft);
-  R* wts = w.wts ? (R*)(ws + w.planes + w.fft + w.acc) : nullptr;
+  R* wts_call = w.wts ? (R*)(ws + w.planes + w.fft + w.acc) : nullptr;   // filled per call
+  R* wts = p->wts_plan ? (R*)p->wts_plan : wts_call;
   int rc = WG_OK;
   IndexView<R> ix{p->off, p->idx, p->meta, (const Z4<R>*)p->z, (const typename C2<R>::T*)p->ph, wts};
   const Coef<R>& coef = *reinterpret_cast<const Coef<R>*>(sizeof(R) == 4 ? (const void*)&p->coef_f
@@ -705,8 +722,8 @@ static int grid_impl(wg_plan* p, const typename C2<R>::T* vis, const R* wgt, R* 
   int64_t nbatches = 0;
   do {
     cudaError_t e = cudaSuccess;
-    if (wts != nullptr) {
-      e = launch_weights<R>(g, coef, ix, p->nvis, wts, s);
+    if (wts_call != nullptr) {
+      e = launch_weights<R>(g, coef, ix, p->nvis, wts_call, s);
       if (e != cudaSuccess) { rc = set_error(WG_ERR_CUDA, "weights: %s", cudaGetErrorString(e)); break; }
     }
     for (int64_t b0 = 0; b0 < g.nw; b0 += p->batch) {
@@ -731,7 +748,7 @@ static int grid_impl(wg_plan* p, const typename C2<R>::T* vis, const R* wgt, R* 
     tm.finish(stats);
     stats->n_batches = nbatches; stats->n_planes = g.nw; stats->workspace_bytes = w.total;
     // grid + accumulate per batch, weights; the double-float FFT's two passes per batch
-    stats->n_kernels = 2 * nbatches + (wts != nullptr) + (p->dfft != nullptr ? 2 * nbatches : 0);
+    stats->n_kernels = 2 * nbatches + (wts_call != nullptr) + (p->dfft != nullptr ? 2 * nbatches : 0);
     stats->n_fft_calls = nbatches;
   }
   return WG_OK;
