@@ -38,6 +38,38 @@ __device__ __forceinline__ R kernel_value(const IndexView<R>& ix, const R* __res
   return horner(sc, deg, j, z);
 }
 
+// The coefficients of one kernel piece held in a lane's registers (FP32 kernels, where a lane
+// evaluates the same piece for every visibility it handles): zero-padded up to degree G + 3
+// (alpha <= G), so Horner runs a fixed number of steps with no shared-memory loads.
+template <typename R, int G>
+struct LanePiece {
+  static constexpr int kDeg = G + 3;
+  R c[kDeg + 1];
+  __device__ __forceinline__ void load(const R* __restrict__ sc, int deg, int j) {
+#pragma unroll
+    for (int d = 0; d <= kDeg; ++d) c[d] = d <= deg ? sc[d * kMaxG + j] : (R)0;
+  }
+  __device__ __forceinline__ R eval(R z) const {
+    R r = c[kDeg];
+#pragma unroll
+    for (int d = kDeg - 1; d >= 0; --d) r = fma(r, z, c[d]);
+    return r;
+  }
+};
+// register pieces for FP32 only (an FP64 piece would take 40 registers; FP64 plans read the
+// per-call or plan-resident value table, or Horner from shared memory)
+template <typename R, int G>
+using LanePieceOf = LanePiece<R, sizeof(R) == 4 ? G : 0>;
+
+template <typename R, int G>
+__device__ __forceinline__ R kernel_value(const IndexView<R>& ix, const LanePieceOf<R, G>& pc,
+                                          const R* __restrict__ sc, int deg, uint32_t vi, int d,
+                                          int j, R z) {
+  if (ix.wts != nullptr) return ix.wts[(int64_t)vi * (3 * kMaxG) + d * kMaxG + j];
+  if (sizeof(R) == 4) return pc.eval(z);
+  return horner(sc, deg, j, z);
+}
+
 template <int G>
 __device__ __forceinline__ unsigned group_mask() {
   const int lane = threadIdx.x & 31;
@@ -95,6 +127,8 @@ k_degrid(const Geom g, const __grid_constant__ Coef<R> coef, const IndexView<R> 
   // loop runs over the union of the warp's ranges (warp-uniform bounds, per-group predicate)
   // instead of all G candidate planes.
   const int j = threadIdx.x & (G - 1);
+  LanePieceOf<R, G> pc;
+  if (sizeof(R) == 4) pc.load(sc, g.deg, j);
   const int grp = threadIdx.x / G, ngrp = blockDim.x / G;
   const unsigned gmask = group_mask<G>();
   for (uint32_t v0 = lo + (threadIdx.x >> 5) * (32 / G); v0 < hi; v0 += ngrp) {
@@ -106,9 +140,10 @@ k_degrid(const Geom g, const __grid_constant__ Coef<R> coef, const IndexView<R> 
     if (act) { mt = ix.meta[vi]; zz = ix.z[vi]; }
     const int du = mt & 255, dv = (mt >> 8) & 255, c0 = (int)(mt >> 16);
     const bool lj = act && j < alpha;
-    R pu = lj ? kernel_value(ix, sc, g.deg, vi, 0, j, zz.u) : (R)0;
-    R pv = lj ? kernel_value(ix, sc, g.deg, vi, 1, j, zz.v) : (R)0;
-    R pw = g.do_w ? (lj ? kernel_value(ix, sc, g.deg, vi, 2, j, zz.w) : (R)0) : (j == 0 ? (R)1 : (R)0);
+    R pu = lj ? kernel_value<R, G>(ix, pc, sc, g.deg, vi, 0, j, zz.u) : (R)0;
+    R pv = lj ? kernel_value<R, G>(ix, pc, sc, g.deg, vi, 1, j, zz.v) : (R)0;
+    R pw = g.do_w ? (lj ? kernel_value<R, G>(ix, pc, sc, g.deg, vi, 2, j, zz.w) : (R)0)
+                  : (j == 0 ? (R)1 : (R)0);
     R wu[G];
 #pragma unroll
     for (int i = 0; i < G; ++i) wu[i] = __shfl_sync(0xffffffffu, pu, i, G);
@@ -271,6 +306,9 @@ k_grid_owner(const Geom g, const __grid_constant__ Coef<R> coef, const IndexView
   // phase-1 mapping: groups of G lanes, one visibility each
   const int j1 = threadIdx.x & (G - 1), grp = threadIdx.x / G, ngrp = blockDim.x / G;
   const unsigned gmask = group_mask<G>();
+  __syncthreads();   // coefficients staged
+  LanePieceOf<R, G> pc;
+  if (sizeof(R) == 4) pc.load(sc, g.deg, j1);
 
   for (int src = 0; src < 4; ++src) {
     const int ou = (src & 1) ? -1 : 0, ov = (src & 2) ? -1 : 0;
@@ -294,9 +332,9 @@ k_grid_owner(const Geom g, const __grid_constant__ Coef<R> coef, const IndexView
         if (!hit) continue;   // uniform within the group
         const Z4<R> zz = ix.z[vi];
         const bool lj = j1 < alpha;
-        stg->wu[v][j1] = lj ? kernel_value(ix, sc, g.deg, vi, 0, j1, zz.u) : (R)0;
-        stg->wv[v][j1] = lj ? kernel_value(ix, sc, g.deg, vi, 1, j1, zz.v) : (R)0;
-        const R wwj = g.do_w ? (lj ? kernel_value(ix, sc, g.deg, vi, 2, j1, zz.w) : (R)0)
+        stg->wu[v][j1] = lj ? kernel_value<R, G>(ix, pc, sc, g.deg, vi, 0, j1, zz.u) : (R)0;
+        stg->wv[v][j1] = lj ? kernel_value<R, G>(ix, pc, sc, g.deg, vi, 1, j1, zz.v) : (R)0;
+        const R wwj = g.do_w ? (lj ? kernel_value<R, G>(ix, pc, sc, g.deg, vi, 2, j1, zz.w) : (R)0)
                              : (j1 == 0 ? (R)1 : (R)0);
         R dr = (R)0, di = (R)0;
         if (j1 == 0) {
@@ -393,6 +431,8 @@ k_grid_atomic(const Geom g, const __grid_constant__ Coef<R> coef, const IndexVie
   const int j = threadIdx.x & (G - 1);
   const int grp = threadIdx.x / G, ngrp = blockDim.x / G;
   const int gw = grp % (32 / G);
+  LanePieceOf<R, G> pc;
+  if (sizeof(R) == 4) pc.load(sc, g.deg, j);
 
   // sources: this tile and the tiles one to the left / above / both, whose visibilities'
   // alpha x alpha footprints can reach into this tile (alpha - 1 <= T)
@@ -430,14 +470,16 @@ k_grid_atomic(const Geom g, const __grid_constant__ Coef<R> coef, const IndexVie
         }
       }
       const bool lj = act && j < alpha;
-      R pu = lj ? kernel_value(ix, sc, g.deg, vi, 0, j, zz.u) : (R)0;
-      R pv = lj ? kernel_value(ix, sc, g.deg, vi, 1, j, zz.v) : (R)0;
-      R pw = g.do_w ? (lj ? kernel_value(ix, sc, g.deg, vi, 2, j, zz.w) : (R)0) : (j == 0 ? (R)1 : (R)0);
+      R pu = lj ? kernel_value<R, G>(ix, pc, sc, g.deg, vi, 0, j, zz.u) : (R)0;
+      R pv = lj ? kernel_value<R, G>(ix, pc, sc, g.deg, vi, 1, j, zz.v) : (R)0;
+      R pw = g.do_w ? (lj ? kernel_value<R, G>(ix, pc, sc, g.deg, vi, 2, j, zz.w) : (R)0)
+                    : (j == 0 ? (R)1 : (R)0);
       R wu[G];
 #pragma unroll
       for (int i = 0; i < G; ++i) wu[i] = __shfl_sync(0xffffffffu, pu, i, G);
       const int col = rv + j;
       const bool colok = lj && col >= 0 && col < T;
+      const bool rows_in = ru >= 0 && ru + alpha <= T;
       dr *= pv;
       di *= pv;
       const int qlo = act ? max(0, s0 - c0) : G, qhi = act ? min(aw, s0 + sb - c0) : 0;
@@ -448,12 +490,22 @@ k_grid_atomic(const Geom g, const __grid_constant__ Coef<R> coef, const IndexVie
         if (colok && q >= qlo && q < qhi) {
           const R qr = dr * wq, qi = di * wq;
           CT* base = acc + (c0 + q - s0) * plane_elems + col;
+          if (rows_in) {   // the footprint's rows all fall in the tile (the common case)
 #pragma unroll
-          for (int i = 0; i < G; ++i) {
-            const int row = ru + i;
-            if (i < alpha && row >= 0 && row < T) {
-              atomicAdd(&base[row * pitch].x, qr * wu[i]);
-              atomicAdd(&base[row * pitch].y, qi * wu[i]);
+            for (int i = 0; i < G; ++i) {
+              if (i < alpha) {
+                atomicAdd(&base[(ru + i) * pitch].x, qr * wu[i]);
+                atomicAdd(&base[(ru + i) * pitch].y, qi * wu[i]);
+              }
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < G; ++i) {
+              const int row = ru + i;
+              if (i < alpha && row >= 0 && row < T) {
+                atomicAdd(&base[row * pitch].x, qr * wu[i]);
+                atomicAdd(&base[row * pitch].y, qi * wu[i]);
+              }
             }
           }
         }
