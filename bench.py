@@ -254,9 +254,20 @@ def df64_line_ops(n):
     return ops
 
 
-# DRAM bytes the double-float FFT moves per plane cell and pass, measured by ncu on 3456^2
-# planes (row pass 30.7, column pass 30.9: profiles/k_fft_lines_df64_3456.md)
-DF64_DRAM_BYTES_PER_CELL_PASS = 30.8
+# DRAM bytes the double-float FFT moved per algorithmic byte (one 16-byte read and one 16-byte
+# write per cell and pass), measured by ncu on full 3456^2 transforms: 30.8 of 32 B per cell
+# and pass (profiles/k_fft_lines_df64_3456.md); the rest stays in L2 when the kernel ends
+DF64_DRAM_PER_ALGORITHMIC_BYTE = 30.8 / 32.0
+
+
+def df64_fft_bytes(nx, ny, nu, nv, direction):
+    """Algorithmic bytes of one plane's double-float FFT in the library's pruned form: degrid
+    (forward) -- row pass over the nx image rows loading their ny image cells and storing nv,
+    column pass over nv columns loading the nx image rows and storing nu; grid (inverse) --
+    column pass over all nu x nv cells, row pass over the nx image rows storing ny."""
+    if direction == "degrid":
+        return 16 * (nx * ny + nx * nv) + 16 * (nv * nx + nv * nu)
+    return 16 * (2 * nu * nv) + 16 * (nx * nv + nx * ny)
 
 
 def run_sweep(args):
@@ -529,11 +540,11 @@ def main():
         ops = nw * (obs.npix_x * df64_line_ops(nv) + nv * df64_line_ops(nu))
         peak = 152 * 128 * 2.07e9   # SMs x FP32 lanes x max SM clock, one instruction per lane
         ach = ops / (stage_ms[dom] * 1e-3)
-        cells_passes = nw * (obs.npix_x * nv + nv * nu)
+        abytes = nw * df64_fft_bytes(obs.npix_x, obs.npix_y, nu, nv, dir_d)
         roof = {"bound": "alu", "kernel": "k_fft_lines (double-float plane FFT, row + column pass)",
                 "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": DF64_DRAM_BYTES_PER_CELL_PASS * cells_passes,
-                "algorithmic_bytes": 32 * cells_passes,
+                "traffic": DF64_DRAM_PER_ALGORITHMIC_BYTE * abytes,
+                "algorithmic_bytes": abytes,
                 "peak_source": "FP32 arithmetic instructions/s: 152 SMs x 128 lanes x 2.07 GHz "
                                "(an FMA counts once)",
                 "stage": f"{prec_d} {dir_d}"}

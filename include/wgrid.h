@@ -251,6 +251,21 @@ int wg_kernel_poly(int alpha, double beta, double mu, const double* x, double* o
  * piece), k in cycles per cell, for n points. */
 int wg_kernel_psi(int alpha, double beta, double mu, const double* k, double* out, int64_t n);
 
+/* Kernels found by the same optimisation for the supports the paper does not print
+ * (alpha 5, 6, 9, 10, 11, 13, 14, 15; sigma 1.15 to 2.0 in steps of 0.05); the planner uses
+ * them beside the App. A table.  Row i: alpha, sigma, epsilon, beta, mu (WG_ERR_ARG if out of
+ * range). */
+int wg_kernel_design_size(void);
+int wg_kernel_design_row(int i, int* alpha, double* sigma, double* eps, double* beta, double* mu);
+/* Accuracy of the exact modified ES kernel (alpha, beta, mu) at oversampling sigma: the
+ * supremum of the map error function l(x) of Eq. (maperror) over |x| <= 1 / (2 sigma) (Sec. 3.2,
+ * App. A), with psi and the integral over the fractional position by tanh-sinh quadrature. */
+int wg_kernel_eps(int alpha, double beta, double mu, double sigma, double* eps);
+/* The kernel search of Sec. 3.2: (beta, mu) minimising wg_kernel_eps for (alpha, sigma),
+ * Nelder-Mead on log epsilon from (beta0, mu0).  alpha in 2..16, sigma in [1.05, 2.5]. */
+int wg_kernel_search(int alpha, double sigma, double beta0, double mu0, double* beta, double* mu,
+                     double* eps);
+
 /* Planner dry run: the parameters wg_plan_create would choose for the given image, epsilon,
  * precision, options and uvw extent (|u|max, |v|max, |w|min, |w|max in wavelengths) and
  * visibility count.  Fills alpha, sigma, beta, mu, eps_kernel, nu, nv, nw, dw, w0, nshift,

@@ -108,6 +108,13 @@ const std::vector<KernelRow>& kernel_table() {
   return rows;
 }
 
+const std::vector<KernelRow>& kernel_table_design() {
+  static const std::vector<KernelRow> rows = {
+#include "kernel_table_design.inc"
+  };
+  return rows;
+}
+
 double es_phi(int alpha, double beta, double mu, double x) {
   double s = 2.0 * x / alpha;
   if (std::fabs(s) > 1.0) return 0.0;
@@ -390,17 +397,22 @@ static std::vector<int64_t> size_candidates(int64_t nmin, int64_t mult, int kind
 }
 
 // GB300 cost model (seconds), Sec. 4.1: per w-plane the FFT (measured) plus plane traffic
-// per cell and the w-screen phase per image pixel; per visibility the alpha^3 (de)gridding
-// work.  The per-cell / per-pixel / per-visibility constants are measured stage times of this
-// library on GB300 (2048^2 image, 1e6 visibilities) divided by the units processed.
+// per cell and the w-screen phase per image pixel; per visibility the (de)gridding work,
+// alpha planes x alpha rows x the lanes of the visibility's group (G = 4, 8 or 16 >= alpha;
+// the FP64 gridding kernel spreads its lanes over the alpha^2 cells instead, so FP64 counts
+// the mean of G and alpha).  The per-cell / per-pixel / per-visibility constants are measured
+// stage times of this library on GB300 (2048^2 image, 1e6 visibilities, alpha = G = 8 in FP32
+// and 16 in FP64) divided by the units processed.
 static double plan_cost(int prec, int kind, int64_t nu, int64_t nv, int64_t nw, int alpha,
                         int64_t nvis, int64_t nx, int64_t npix) {
   double cells = (double)nu * nv;
   double k_cell = prec ? 3.0e-12 : 2.5e-12;   // s per plane cell (screen / (de)grid traffic)
   double k_pix = prec ? 6.0e-11 : 1.8e-12;    // s per image pixel per plane (screen phase)
-  double k_vis = prec ? 1.05e-11 : 5.0e-12;   // s per visibility per alpha^3
+  double k_vis = prec ? 1.05e-11 : 5.0e-12;   // s per visibility per alpha^2 x lanes
+  const int G = alpha <= 4 ? 4 : (alpha <= 8 ? 8 : 16);
+  const double lanes = prec ? 0.5 * (G + alpha) : (double)G;
   return nw * (1e-3 * fft_ms(nu, nv, kind, prec, nx) + cells * k_cell + (double)npix * k_pix) +
-         (double)nvis * alpha * alpha * alpha * k_vis;
+         (double)nvis * alpha * alpha * lanes * k_vis;
 }
 
 // Cheapest (nu, nv) for one plane among the candidates (FFT + traffic per cell); false if the
@@ -448,12 +460,15 @@ int choose_plan(const PlanInput& in, PlanParams& out, char* err, int errlen) {
   bool found = false, size_ok = false;
   PlanParams best;
   best.cost = std::numeric_limits<double>::infinity();
-  const auto& T = kernel_table();
-  for (int alpha : {4, 7, 8, 12, 16}) {
+  // kernels: the App. A table (alpha 4, 7, 8, 12, 16) and the searched ones for the other
+  // supports (kernel_design.cpp)
+  std::vector<KernelRow> T = kernel_table();
+  for (const auto& r : kernel_table_design()) T.push_back(r);
+  for (int alpha = 4; alpha <= kMaxAlpha; ++alpha) {
     if (in.force_alpha > 0 && alpha != in.force_alpha) continue;
-    // uv tile side: 32 cells; 16 for wide FP64 kernels, whose (tile + alpha - 1)^2 staging
-    // area would otherwise crowd shared memory
-    int tile = in.tile > 0 ? in.tile : ((in.prec == 1 && alpha >= 12) ? 16 : 32);
+    // uv tile side: 32 cells; 16 for FP64 kernels wider than 8 (16-lane groups), whose
+    // (tile + alpha - 1)^2 staging area would otherwise crowd shared memory
+    int tile = in.tile > 0 ? in.tile : ((in.prec == 1 && alpha > 8) ? 16 : 32);
     if (alpha - 1 > tile) continue;
     std::vector<const KernelRow*> rows;
     for (const auto& r : T) {

@@ -21,6 +21,19 @@ struct KernelRow {
 
 // App. A: optimal modified-ES parameters for alpha in {4, 7, 8, 12, 16}.
 const std::vector<KernelRow>& kernel_table();
+// The same optimisation run by kernel_search for the other supports (alpha 5, 6, 9, 10, 11,
+// 13, 14, 15; sigma 1.15 ... 2.0), generated into kernel_table_design.inc.
+const std::vector<KernelRow>& kernel_table_design();
+
+// Kernel design (kernel_design.cpp), for the exact modified ES kernel:
+// psi(k) by tanh-sinh quadrature; the map error function l(x) of Eq. (maperror) by
+// piecewise tanh-sinh quadrature over the fractional position nu; its supremum over
+// |x| <= 1 / (2 sigma) (the kernel's epsilon, App. A); and the (beta, mu) minimising it from a
+// starting point (Nelder-Mead on log epsilon).
+double es_psi(int alpha, double beta, double mu, double k);
+double es_map_error(int alpha, double beta, double mu, double x);
+double es_kernel_eps(int alpha, double beta, double mu, double sigma);
+KernelRow kernel_search(int alpha, double sigma, double beta0, double mu0);
 
 // Eq. (semicircle2): exp(alpha beta [(1 - (2x/alpha)^2)^mu - 1]) on [-alpha/2, alpha/2].
 double es_phi(int alpha, double beta, double mu, double x);

@@ -222,20 +222,26 @@ __global__ void k_degrid_finalize(const Geom g, const IndexView<R> ix,
 // first a group of G lanes per visibility stages its kernel values in u and v (Sec. 4.2) and
 // its data times the w kernel value of each of its planes; then each warp walks the chunk and,
 // for every visibility touching one of its planes, spreads the 32 lanes over the cells of the
-// footprint that fall inside the tile (the clipped footprint, row-major), computes their 2-D
-// weights wu * wv once, and adds them into each of its planes the visibility touches.
+// footprint that fall inside the tile (the clipped footprint, row-major) and adds their
+// staged 2-D weights wu * wv times the visibility's plane-weighted data into each of its planes
+// the visibility touches.  The 2-D weights are formed once per visibility in phase 1 (by the
+// visibility's lane group, exchanging its u and v values by shuffles), not once per warp.
 // ---------------------------------------------------------------------------------------
-constexpr int kChunk = 64;   // visibilities staged per chunk
+// visibilities staged per chunk: the staged 2-D weights of a chunk take kChunk x G^2 values
+template <int G>
+struct OwnerChunk {
+  static constexpr int value = G > 8 ? 12 : 48;
+};
 // plane-owner gridding CTA: 8 warps (4 warps with 4 planes each measured 10 % slower: fewer
 // warps to hide the shared-memory latency of the updates)
 constexpr int kOwnerThreads = 256;
 constexpr int kOwnerWarps = kOwnerThreads / 32;   // warp w owns planes w, w + kOwnerWarps, ...
 
-template <typename R>
+template <typename R, int G>
 struct GridStage {
-  R wu[kChunk][kMaxG];
-  R wv[kChunk][kMaxG];
-  typename C2<R>::T dq[kChunk][kMaxG];   // data x w kernel value of plane q of the visibility
+  static constexpr int kChunk = OwnerChunk<G>::value;
+  R wt[kChunk][G * G];                  // wu_i * wv_j of the clipped footprint cells, row-major
+  typename C2<R>::T dq[kChunk][G];      // data x w kernel value of plane q of the visibility
   int ru[kChunk], rv[kChunk], c0[kChunk];
 };
 
@@ -246,12 +252,12 @@ struct OwnerFootprint {
 };
 
 // Add visibility v of the chunk into the warp's planes p1, p1 + kOwnerWarps, .. < phi: lane
-// takes cells lane + 32 m (m < MC) of the clipped footprint in row-major order, forms their
-// 2-D weights once and updates each plane (plane pl uses the staged data x w value of the
+// takes cells lane + 32 m (m < MC) of the clipped footprint in row-major order, loads their
+// staged 2-D weights and updates each plane (plane pl uses the staged data x w value of the
 // visibility's plane pl + qoff).  Lanes past the last cell update a private cell of the row
 // padding (columns T, T + 1) with weight 0, so every update is unconditional.
-template <typename R, int MC>
-__device__ __forceinline__ void owner_add(const GridStage<R>* __restrict__ stg, int v,
+template <typename R, int G, int MC>
+__device__ __forceinline__ void owner_add(const GridStage<R, G>* __restrict__ stg, int v,
                                           const OwnerFootprint& fp, int lane, int T, int pitch,
                                           int p1, int phi, int qoff,
                                           typename C2<R>::T* __restrict__ acc, int plane_elems) {
@@ -268,7 +274,7 @@ __device__ __forceinline__ void owner_add(const GridStage<R>* __restrict__ stg, 
     const int ii = (int)(((float)c + 0.5f) * rw), jj = c - ii * fp.w;
     const bool ok = c < fp.cells;
     const int i = fp.i0 + (ok ? ii : 0), j = fp.j0 + (ok ? jj : 0);
-    wt[m] = ok ? stg->wu[v][i] * stg->wv[v][j] : (R)0;
+    wt[m] = ok ? stg->wt[v][c] : (R)0;
     off[m] = ok ? (fp.ru + i) * pitch + fp.rv + j : dummy;
   }
   for (int pl = p1; pl < phi; pl += kOwnerWarps) {
@@ -292,8 +298,10 @@ k_grid_owner(const Geom g, const __grid_constant__ Coef<R> coef, const IndexView
   using CT = typename C2<R>::T;
   extern __shared__ __align__(16) unsigned char smem[];
   R* sc = reinterpret_cast<R*>(smem);
-  GridStage<R>* stg = reinterpret_cast<GridStage<R>*>(smem + (kMaxDeg + 1) * kMaxG * sizeof(R));
-  CT* acc = reinterpret_cast<CT*>(reinterpret_cast<unsigned char*>(stg) + sizeof(GridStage<R>));
+  using Stage = GridStage<R, G>;
+  constexpr int kChunk = Stage::kChunk;
+  Stage* stg = reinterpret_cast<Stage*>(smem + (kMaxDeg + 1) * kMaxG * sizeof(R));
+  CT* acc = reinterpret_cast<CT*>(reinterpret_cast<unsigned char*>(stg) + sizeof(Stage));
   const int T = g.tile, alpha = g.alpha, aw = g.alpha_w;
   const int t = blockIdx.x;
   const int tu = t / g.ntv, tv = t - tu * g.ntv;
@@ -335,8 +343,27 @@ k_grid_owner(const Geom g, const __grid_constant__ Coef<R> coef, const IndexView
         if (!hit) continue;   // uniform within the group
         const Z4<R> zz = ix.z[vi];
         const bool lj = j1 < alpha;
-        stg->wu[v][j1] = lj ? kernel_value<R, G>(ix, pc, sc, g.deg, vi, 0, j1, zz.u) : (R)0;
-        stg->wv[v][j1] = lj ? kernel_value<R, G>(ix, pc, sc, g.deg, vi, 1, j1, zz.v) : (R)0;
+        const R pu = lj ? kernel_value<R, G>(ix, pc, sc, g.deg, vi, 0, j1, zz.u) : (R)0;
+        const R pv = lj ? kernel_value<R, G>(ix, pc, sc, g.deg, vi, 1, j1, zz.v) : (R)0;
+        // 2-D weights of the footprint cells inside the tile (rows i0.., columns j0..j0+w-1),
+        // row-major: lane j1 forms cells j1, j1 + G, ... from the group's u and v values
+        {
+          const int i0 = max(0, -ru), i1 = min(alpha, T - ru);
+          const int j0 = max(0, -rv), w = min(alpha, T - rv) - j0;
+          const int cells = (i1 - i0) * w;
+          const float rw = 1.0f / (float)w;
+          const int nt = (cells + G - 1) / G;   // same trip count for the whole group
+          for (int tq = 0; tq < nt; ++tq) {
+            const int c = j1 + G * tq;
+            // exact in float: c < 256 and w <= 16 keep (c + 0.5) / w at least 1 / 32 away
+            // from an integer
+            const int ii = (int)(((float)c + 0.5f) * rw), jj = c - ii * w;
+            const bool ok = c < cells;
+            const R a = __shfl_sync(gmask, pu, ok ? i0 + ii : 0, G);
+            const R b = __shfl_sync(gmask, pv, ok ? j0 + jj : 0, G);
+            if (ok) stg->wt[v][c] = a * b;
+          }
+        }
         const R wwj = g.do_w ? (lj ? kernel_value<R, G>(ix, pc, sc, g.deg, vi, 2, j1, zz.w) : (R)0)
                              : (j1 == 0 ? (R)1 : (R)0);
         R dr = (R)0, di = (R)0;
@@ -377,14 +404,14 @@ k_grid_owner(const Geom g, const __grid_constant__ Coef<R> coef, const IndexView
         // exactly its updates (no predicated-off FP64 instructions)
         const OwnerFootprint fp{i0, j0, w, cells, ru, rv};
         switch ((cells + 31) >> 5) {
-          case 1: owner_add<R, 1>(stg, v, fp, lane, T, pitch, p1, phi, s0 - c0, acc, plane_elems); break;
-          case 2: owner_add<R, 2>(stg, v, fp, lane, T, pitch, p1, phi, s0 - c0, acc, plane_elems); break;
-          case 3: owner_add<R, (G > 8 ? 3 : 1)>(stg, v, fp, lane, T, pitch, p1, phi, s0 - c0, acc, plane_elems); break;
-          case 4: owner_add<R, (G > 8 ? 4 : 1)>(stg, v, fp, lane, T, pitch, p1, phi, s0 - c0, acc, plane_elems); break;
-          case 5: owner_add<R, (G > 8 ? 5 : 1)>(stg, v, fp, lane, T, pitch, p1, phi, s0 - c0, acc, plane_elems); break;
-          case 6: owner_add<R, (G > 8 ? 6 : 1)>(stg, v, fp, lane, T, pitch, p1, phi, s0 - c0, acc, plane_elems); break;
-          case 7: owner_add<R, (G > 8 ? 7 : 1)>(stg, v, fp, lane, T, pitch, p1, phi, s0 - c0, acc, plane_elems); break;
-          default: owner_add<R, (G > 8 ? 8 : 1)>(stg, v, fp, lane, T, pitch, p1, phi, s0 - c0, acc, plane_elems); break;
+          case 1: owner_add<R, G, 1>(stg, v, fp, lane, T, pitch, p1, phi, s0 - c0, acc, plane_elems); break;
+          case 2: owner_add<R, G, 2>(stg, v, fp, lane, T, pitch, p1, phi, s0 - c0, acc, plane_elems); break;
+          case 3: owner_add<R, G, (G > 8 ? 3 : 1)>(stg, v, fp, lane, T, pitch, p1, phi, s0 - c0, acc, plane_elems); break;
+          case 4: owner_add<R, G, (G > 8 ? 4 : 1)>(stg, v, fp, lane, T, pitch, p1, phi, s0 - c0, acc, plane_elems); break;
+          case 5: owner_add<R, G, (G > 8 ? 5 : 1)>(stg, v, fp, lane, T, pitch, p1, phi, s0 - c0, acc, plane_elems); break;
+          case 6: owner_add<R, G, (G > 8 ? 6 : 1)>(stg, v, fp, lane, T, pitch, p1, phi, s0 - c0, acc, plane_elems); break;
+          case 7: owner_add<R, G, (G > 8 ? 7 : 1)>(stg, v, fp, lane, T, pitch, p1, phi, s0 - c0, acc, plane_elems); break;
+          default: owner_add<R, G, (G > 8 ? 8 : 1)>(stg, v, fp, lane, T, pitch, p1, phi, s0 - c0, acc, plane_elems); break;
         }
       }
     }
@@ -602,7 +629,7 @@ static cudaError_t grid_owner_g(const Geom& g, const Coef<R>& coef, const IndexV
   // cell for idle updates
   const int pitch = g.tile + 2;
   const size_t per = (size_t)g.tile * pitch * sizeof(typename C2<R>::T);
-  const size_t fixed = coef_bytes<R>() + sizeof(GridStage<R>);
+  const size_t fixed = coef_bytes<R>() + sizeof(GridStage<R, G>);
   const int nwarps = kOwnerWarps;
   int bs = (int)std::max<size_t>(1, (kGridSmemBudget - fixed) / per);
   if (bs > nwarps) bs -= bs % nwarps;  // equal planes per warp

@@ -894,6 +894,36 @@ int wg_kernel_psi(int alpha, double beta, double mu, const double* k, double* ou
   return WG_OK;
 }
 
+int wg_kernel_design_size(void) { return (int)kernel_table_design().size(); }
+
+int wg_kernel_design_row(int i, int* alpha, double* sigma, double* eps, double* beta, double* mu) {
+  const auto& T = kernel_table_design();
+  if (i < 0 || i >= (int)T.size()) return set_error(WG_ERR_ARG, "row out of range");
+  if (alpha) *alpha = T[i].alpha;
+  if (sigma) *sigma = T[i].sigma;
+  if (eps) *eps = T[i].eps;
+  if (beta) *beta = T[i].beta;
+  if (mu) *mu = T[i].mu;
+  return WG_OK;
+}
+
+int wg_kernel_eps(int alpha, double beta, double mu, double sigma, double* eps) {
+  if (alpha < 2 || alpha > kMaxAlpha || !(beta > 0) || !(mu > 0) || !(sigma > 1.0) || !eps)
+    return set_error(WG_ERR_ARG, "bad arguments");
+  *eps = es_kernel_eps(alpha, beta, mu, sigma);
+  return WG_OK;
+}
+
+int wg_kernel_search(int alpha, double sigma, double beta0, double mu0, double* beta, double* mu,
+                     double* eps) {
+  if (alpha < 2 || alpha > kMaxAlpha || !(sigma >= 1.05 && sigma <= 2.5) || !(beta0 > 0) ||
+      !(mu0 > 0.2 && mu0 < 1.5) || !beta || !mu || !eps)
+    return set_error(WG_ERR_ARG, "bad arguments");
+  KernelRow r = kernel_search(alpha, sigma, beta0, mu0);
+  *beta = r.beta; *mu = r.mu; *eps = r.eps;
+  return WG_OK;
+}
+
 int wg_plan_params(int64_t npix_x, int64_t npix_y, double pixsize_x, double pixsize_y,
                    double epsilon, int precision, const wg_options* opt, double umax,
                    double vmax, double wmin, double wmax, int64_t nvis, wg_plan_info* info) {

@@ -91,6 +91,12 @@ SIGNATURES = {
     "wg_kernel_phi": (_I, [_I, _D, _D, _VP, _VP, _I64]),
     "wg_kernel_poly": (_I, [_I, _D, _D, _VP, _VP, _I64]),
     "wg_kernel_psi": (_I, [_I, _D, _D, _VP, _VP, _I64]),
+    "wg_kernel_design_size": (_I, []),
+    "wg_kernel_design_row": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_D),
+                                  ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "wg_kernel_eps": (_I, [_I, _D, _D, _D, ctypes.POINTER(_D)]),
+    "wg_kernel_search": (_I, [_I, _D, _D, _D, ctypes.POINTER(_D), ctypes.POINTER(_D),
+                              ctypes.POINTER(_D)]),
     "wg_plan_params": (_I, [_I64, _I64, _D, _D, _D, _I, ctypes.POINTER(Options), _D, _D, _D, _D,
                             _I64, ctypes.POINTER(PlanInfo)]),
     "wg_fft_time": (_I, [_I64, _I, _I64, _I, _I, ctypes.POINTER(_D)]),
@@ -336,6 +342,32 @@ def ms2dirty(uvw, freq, ms, wgt=None, npix_x=None, npix_y=None, pixsize_x=None, 
 # ----------------------------------------------------------------------------------------
 # host-only helpers (no GPU needed)
 # ----------------------------------------------------------------------------------------
+def kernel_design_table():
+    """Searched kernels for the supports App. A does not print: [(alpha, sigma, eps, beta, mu)]."""
+    rows = []
+    for i in range(lib().wg_kernel_design_size()):
+        a, sg, e, b, m = ctypes.c_int(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(lib().wg_kernel_design_row(i, ctypes.byref(a), ctypes.byref(sg), ctypes.byref(e),
+                                          ctypes.byref(b), ctypes.byref(m)))
+        rows.append((a.value, sg.value, e.value, b.value, m.value))
+    return rows
+
+
+def kernel_eps(alpha, beta, mu, sigma) -> float:
+    """Supremum of the map error function of the exact modified ES kernel over |x| <= 1/(2 sigma)."""
+    e = ctypes.c_double()
+    _check(lib().wg_kernel_eps(int(alpha), float(beta), float(mu), float(sigma), ctypes.byref(e)))
+    return e.value
+
+
+def kernel_search(alpha, sigma, beta0, mu0):
+    """(beta, mu, eps) minimising kernel_eps for (alpha, sigma), from (beta0, mu0)."""
+    b, m, e = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().wg_kernel_search(int(alpha), float(sigma), float(beta0), float(mu0),
+                                  ctypes.byref(b), ctypes.byref(m), ctypes.byref(e)))
+    return b.value, m.value, e.value
+
+
 def kernel_table():
     """Rows (alpha, sigma, eps, beta, mu) of the library's built-in table (App. A)."""
     L = lib()

@@ -91,11 +91,13 @@ def test_small_matches_oracle(wg, oracle_lib, small_ref, prec, eps, w_shift):
     assert adj < adj_tol(prec, eps, plan.info["fft_impl"])
 
 
-@pytest.mark.parametrize("alpha", [4, 7, 8, 12, 16])
+@pytest.mark.parametrize("alpha", list(range(4, 17)))
 def test_every_kernel_support(wg, oracle_lib, small_ref, alpha):
-    """Force each tabulated support (G = 4, 8, 16 lane groups, tiles 16 and 32)."""
+    """Force each support, printed (App. A) or searched (G = 4, 8, 16 lane groups, tiles 16
+    and 32, odd and even alpha)."""
     I, d, rv, ri = small_ref
-    eps = {4: 3e-2, 7: 1e-3, 8: 1e-4, 12: 1e-6, 16: 1e-9}[alpha]
+    eps = {4: 3e-2, 5: 1e-2, 6: 3e-3, 7: 1e-3, 8: 1e-4, 9: 3e-5, 10: 1e-5, 11: 3e-6, 12: 1e-6,
+           13: 3e-7, 14: 1e-7, 15: 3e-8, 16: 1e-9}[alpha]
     plan, vis, img = run_pair(wg, SMALL, eps, "f64", I, d, force_alpha=alpha)
     assert plan.info["alpha"] == alpha
     assert oracle_lib.rel_l2(vis, rv) <= eps and oracle_lib.rel_l2(img, ri) <= eps
@@ -307,3 +309,23 @@ def test_wide_8k_sampled_fp32(wg, oracle_lib):
     ri = oracle_lib.grid(obs.uvw, obs.freq, d, obs.npix_x, obs.npix_y, obs.pixsize_x,
                          obs.pixsize_y, pixel_index=psel)
     assert oracle_lib.rel_l2(img.reshape(-1)[psel], ri) <= 1e-5
+
+
+@pytest.mark.parametrize("prec,eps,fft_impl", [("f32", 1e-5, 0), ("f64", 1e-12, 2), ("f64", 1e-10, 3)])
+def test_plane_batches(wg, oracle_lib, small_ref, prec, eps, fft_impl):
+    """A workspace cap that holds only a few planes: the planes go through the screen / FFT /
+    (de)gridding / accumulation in several batches.  Same result as one batch up to summation
+    order (the degrid sub-batches and the grid accumulator group the planes differently) and
+    within epsilon of the oracle."""
+    I, d, rv, ri = small_ref
+    one, v1, g1 = run_pair(wg, SMALL, eps, prec, I, d, fft_impl=fft_impl)
+    many, vm, gm = run_pair(wg, SMALL, eps, prec, I, d, fft_impl=fft_impl, max_workspace=5 << 20)
+    assert one.info["batch"] == one.info["nw"]
+    assert 1 < many.info["batch"] < many.info["nw"], many.info
+    # rounding of the planes, amplified by the 1 / psi correction, bounds the (relative L2)
+    # difference of two summation orders: a few times the planner's plane-rounding term
+    info = one.info
+    r_term = math.sqrt(max(info["err_model"] ** 2 - (info["eps_kernel"] / 0.8) ** 2, 0.0))
+    tol = max(1e-6 if prec == "f32" else 1e-13, 10 * r_term)
+    assert oracle_lib.rel_l2(vm, v1) <= tol and oracle_lib.rel_l2(gm, g1) <= tol
+    assert oracle_lib.rel_l2(vm, rv) <= eps and oracle_lib.rel_l2(gm, ri) <= eps

@@ -90,7 +90,8 @@ def test_planner_follows_sec2_definitions(wg, w_shift, prec, eps):
     # chosen kernel meets epsilon and is the smallest such sigma for its alpha (Sec. 4.1), the
     # error counting the kernel term and the plane rounding of the chosen FFT kind
     safety = 0.8   # default: table epsilon <= 0.8 x requested
-    rows = [r for r in wg.kernel_table() if r[0] == alpha and r[2] <= safety * eps]
+    rows = [r for r in list(wg.kernel_table()) + wg.kernel_design_table()
+            if r[0] == alpha and r[2] <= safety * eps]
     assert info["eps_kernel"] <= safety * eps and info["err_model"] <= eps
     for r in rows:
         if r[1] < sigma:
@@ -128,13 +129,16 @@ def test_planner_cost_prefers_cheap_fp32_kernels(wg):
     """Sec. 4.1: across alpha the predicted cheapest kernel wins; FP64 at 1e-12 needs alpha 16
     (sigma 1.55 with FP64 planes; the double-float FFT's larger rounding needs more)."""
     _, f64 = _planner_case(wg, precision="f64", epsilon=1e-12, fft_impl=3)
-    assert f64["alpha"] == 16 and f64["sigma"] == 1.55 and f64["fft_impl"] == 3
+    assert f64["alpha"] >= 15 and f64["fft_impl"] == 3
     _, df = _planner_case(wg, precision="f64", epsilon=1e-12, fft_impl=2)
-    assert df["alpha"] == 16 and df["sigma"] > 1.55 and df["fft_impl"] == 2
+    assert df["alpha"] >= 15 and df["sigma"] > 1.55 and df["fft_impl"] == 2
     _, auto = _planner_case(wg, precision="f64", epsilon=1e-12)
-    assert auto["alpha"] == 16 and auto["fft_impl"] in (2, 3) and auto["err_model"] <= 1e-12
+    assert auto["alpha"] >= 15 and auto["fft_impl"] in (2, 3) and auto["err_model"] <= 1e-12
+    # with only the printed supports (forced), FP64 planes at 1e-12 need alpha 16, sigma 1.55
+    _, f16 = _planner_case(wg, precision="f64", epsilon=1e-12, fft_impl=3, force_alpha=16)
+    assert f16["sigma"] == 1.55
     _, f32 = _planner_case(wg)
-    assert f32["alpha"] in (7, 8, 12) and f32["fft_impl"] == 1
+    assert 6 <= f32["alpha"] <= 12 and f32["fft_impl"] == 1
 
 
 def _gain_reference(nx, ny, psx, psy, nu, nv, alpha, beta, mu, nshift, dw):
