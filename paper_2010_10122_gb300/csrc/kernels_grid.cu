@@ -429,40 +429,46 @@ k_grid_owner(const Geom g, const __grid_constant__ Coef<R> coef, const IndexView
 // ---------------------------------------------------------------------------------------
 // grid, shared-atomic variant (default for FP32)
 //
-// CTA = (uv tile, sub-batch of planes), owning the T x T cells of those planes.  A group of G
-// lanes handles one visibility (lane j = footprint column j) and adds its contributions with
-// shared-memory float atomics; groups run concurrently, so cells shared by overlapping
-// footprints are combined by the atomics (summation order not fixed).  The plane loop covers the
-// union of the warp's plane ranges (tile-sorted visibilities have nearly equal ranges).
+// CTA = (uv tile, sub-batch of planes), owning the T x T cells of those planes as separate real
+// and imaginary accumulators in shared memory.  A warp handles one visibility at a time: lane
+// (j, rg) = (lane mod G, lane / G) takes footprint column j and rows rg, rg + 32 / G, ...;
+// with the accumulator row pitch = G (mod 32), the 32 lanes of every atomic add hit 32
+// different banks.  Kernel values (Sec. 4.2): each lane evaluates piece j in u (rg = 0) or v
+// (rg > 0) and in w, and the warp exchanges them by shuffles.  Warps run concurrently, so cells
+// shared by overlapping footprints are combined by the atomics (summation order not fixed).
 // ---------------------------------------------------------------------------------------
+template <int G>
+struct AtomicLayout {
+  static constexpr int kRowGroups = 32 / G;                      // rows handled at once
+  static constexpr int kRowsPerLane = G * G / 32 > 0 ? G * G / 32 : 1;   // ceil(G / kRowGroups)
+};
+
 template <typename R, int G>
 __global__ void __launch_bounds__(kThreads)
 k_grid_atomic(const Geom g, const __grid_constant__ Coef<R> coef, const IndexView<R> ix,
               const typename C2<R>::T* __restrict__ vis, const R* __restrict__ wgt,
               typename C2<R>::T* __restrict__ planes, int b0, int nb, int bs, int pitch) {
   using CT = typename C2<R>::T;
+  constexpr int RG = AtomicLayout<G>::kRowGroups;
+  constexpr int KR = AtomicLayout<G>::kRowsPerLane;
   extern __shared__ __align__(16) unsigned char smem[];
   R* sc = reinterpret_cast<R*>(smem);
-  CT* acc = reinterpret_cast<CT*>(smem + (kMaxDeg + 1) * kMaxG * sizeof(R));
+  R* acc = reinterpret_cast<R*>(smem + (kMaxDeg + 1) * kMaxG * sizeof(R));
   const int T = g.tile, alpha = g.alpha, aw = g.alpha_w;
   const int t = blockIdx.x;
   const int tu = t / g.ntv, tv = t - tu * g.ntv;
   const int s0 = b0 + blockIdx.y * bs;
   const int sb = min(bs, b0 + nb - s0);
   const int plane_elems = T * pitch;
+  R* acc_im = acc + sb * plane_elems;   // real parts of the sb planes, then imaginary parts
   for (int i = threadIdx.x; i < (g.deg + 1) * kMaxG; i += blockDim.x) sc[i] = coef.c[i];
-  for (int e = threadIdx.x; e < sb * plane_elems; e += blockDim.x) {
-    CT z; z.x = (R)0; z.y = (R)0;
-    acc[e] = z;
-  }
+  for (int e = threadIdx.x; e < 2 * sb * plane_elems; e += blockDim.x) acc[e] = (R)0;
   __syncthreads();
-  // G lanes per visibility (lane j = piece / footprint column j); plane loop over the union of
-  // the warp's plane ranges (warp-uniform bounds, per-group predicate)
-  const int j = threadIdx.x & (G - 1);
-  const int grp = threadIdx.x / G, ngrp = blockDim.x / G;
-  const int gw = grp % (32 / G);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int j = lane & (G - 1), rg = lane / G;
   LanePieceOf<R, G> pc;
   if (sizeof(R) == 4) pc.load(sc, g.deg, j);
+  const bool lj = j < alpha;
 
   // sources: this tile and the tiles one to the left / above / both, whose visibilities'
   // alpha x alpha footprints can reach into this tile (alpha - 1 <= T)
@@ -472,70 +478,79 @@ k_grid_atomic(const Geom g, const __grid_constant__ Coef<R> coef, const IndexVie
     int stv = tv + ov; if (stv < 0) stv += g.ntv;
     const uint32_t* offs = ix.off + ((int64_t)stu * g.ntv + stv) * g.nw;
     const uint32_t lo = offs[max(0, s0 - aw + 1)], hi = offs[min(g.nw, s0 + sb)];
-    for (uint32_t v0 = lo + (threadIdx.x >> 5) * (32 / G); v0 < hi; v0 += ngrp) {
-      const uint32_t vi = v0 + gw;
-      uint32_t mt = 0;
-      if (vi < hi) mt = ix.meta[vi];
-      const int ru = (int)(mt & 255) + ou * T, rv = (int)((mt >> 8) & 255) + ov * T;
-      // footprint misses this tile (or no visibility for this group)
-      const bool act = vi < hi && ru + alpha > 0 && rv + alpha > 0;
-      if (__all_sync(0xffffffffu, !act)) continue;
-      const int c0 = (int)(mt >> 16);
-      Z4<R> zz;
-      zz.u = zz.v = zz.w = zz.pad = (R)0;
-      R dr = (R)0, di = (R)0;
-      if (act) {
-        zz = ix.z[vi];
-        const uint32_t id = ix.idx[vi];
-        const int64_t k = id & ~kFoldBit;
-        CT d = vis[k];
-        dr = d.x; di = d.y;
-        if (wgt != nullptr) { R w = wgt[k]; dr *= w; di *= w; }
-        if (id & kFoldBit) di = -di;      // grid conj(d) at the folded coordinates
-        if (ix.ph != nullptr) {           // times conj(exp(2 pi i w nshift))
-          CT ph = ix.ph[vi];
-          R r = dr * ph.x + di * ph.y;
-          di = di * ph.x - dr * ph.y;
-          dr = r;
+    // blocks of 32 visibilities per warp, interleaved over the warps (visibility vb + l nwarps
+    // of block vb goes to lane l): each lane loads the coordinates and data of its visibility
+    // (one round trip for 32), then the warp takes the block's visibilities whose footprint
+    // meets the tile one at a time, broadcast by shuffles
+    for (uint32_t vb = lo + warp; vb < hi; vb += 32 * nwarps) {
+      const uint32_t vl = vb + lane * nwarps;
+      uint32_t mtl = 0;
+      Z4<R> zl;
+      zl.u = zl.v = zl.w = zl.pad = (R)0;
+      R drl = (R)0, dil = (R)0;
+      bool hitl = false;
+      if (vl < hi) {
+        mtl = ix.meta[vl];
+        const int ru = (int)(mtl & 255) + ou * T, rv = (int)((mtl >> 8) & 255) + ov * T;
+        hitl = ru + alpha > 0 && rv + alpha > 0;   // footprint meets this tile
+        if (hitl) {
+          zl = ix.z[vl];
+          const uint32_t id = ix.idx[vl];
+          const int64_t k = id & ~kFoldBit;
+          const CT d = vis[k];
+          drl = d.x; dil = d.y;
+          if (wgt != nullptr) { const R w = wgt[k]; drl *= w; dil *= w; }
+          if (id & kFoldBit) dil = -dil;    // grid conj(d) at the folded coordinates
+          if (ix.ph != nullptr) {           // times conj(exp(2 pi i w nshift))
+            const CT ph = ix.ph[vl];
+            const R r = drl * ph.x + dil * ph.y;
+            dil = dil * ph.x - drl * ph.y;
+            drl = r;
+          }
         }
       }
-      const bool lj = act && j < alpha;
-      R pu = lj ? kernel_value<R, G>(ix, pc, sc, g.deg, vi, 0, j, zz.u) : (R)0;
-      R pv = lj ? kernel_value<R, G>(ix, pc, sc, g.deg, vi, 1, j, zz.v) : (R)0;
-      R pw = g.do_w ? (lj ? kernel_value<R, G>(ix, pc, sc, g.deg, vi, 2, j, zz.w) : (R)0)
-                    : (j == 0 ? (R)1 : (R)0);
-      R wu[G];
-#pragma unroll
-      for (int i = 0; i < G; ++i) wu[i] = __shfl_sync(0xffffffffu, pu, i, G);
-      const int col = rv + j;
-      const bool colok = lj && col >= 0 && col < T;
-      const bool rows_in = ru >= 0 && ru + alpha <= T;
-      dr *= pv;
-      di *= pv;
-      const int qlo = act ? max(0, s0 - c0) : G, qhi = act ? min(aw, s0 + sb - c0) : 0;
-      const int wlo = __reduce_min_sync(0xffffffffu, (unsigned)qlo);
-      const int whi = __reduce_max_sync(0xffffffffu, (unsigned)qhi);
-      for (int q = wlo; q < whi; ++q) {
-        const R wq = __shfl_sync(0xffffffffu, pw, q, G);
-        if (colok && q >= qlo && q < qhi) {
+      unsigned hits = __ballot_sync(0xffffffffu, hitl);
+      while (hits != 0u) {
+        const int v = __ffs(hits) - 1;
+        hits &= hits - 1u;
+        const uint32_t vi = vb + v * nwarps;
+        const uint32_t mt = __shfl_sync(0xffffffffu, mtl, v);
+        const int ru = (int)(mt & 255) + ou * T, rv = (int)((mt >> 8) & 255) + ov * T;
+        const int c0 = (int)(mt >> 16);
+        const R zu = __shfl_sync(0xffffffffu, zl.u, v), zv = __shfl_sync(0xffffffffu, zl.v, v);
+        const R zw = __shfl_sync(0xffffffffu, zl.w, v);
+        const R dr = __shfl_sync(0xffffffffu, drl, v), di = __shfl_sync(0xffffffffu, dil, v);
+        // piece j in u (row group 0) or v (the others), and in w
+        const R puv = lj ? kernel_value<R, G>(ix, pc, sc, g.deg, vi, rg == 0 ? 0 : 1, j,
+                                              rg == 0 ? zu : zv) : (R)0;
+        const R pw = g.do_w ? (lj ? kernel_value<R, G>(ix, pc, sc, g.deg, vi, 2, j, zw) : (R)0)
+                            : (j == 0 ? (R)1 : (R)0);
+        // this lane's column weight and the 2-D weights of its rows, clipped to the tile
+        const R pv = __shfl_sync(0xffffffffu, puv, G + j);   // lane G + j holds v piece j
+        const int col = rv + j;
+        const bool colok = lj && col >= 0 && col < T;
+        R cw[KR];
+        int off[KR];
+  #pragma unroll
+        for (int k = 0; k < KR; ++k) {
+          const int i = rg + k * RG;
+          const R pu = __shfl_sync(0xffffffffu, puv, i < G ? i : 0);   // lane i holds u piece i
+          const int row = ru + i;
+          const bool ok = colok && i < alpha && row >= 0 && row < T;
+          cw[k] = ok ? pu * pv : (R)0;
+          off[k] = ok ? row * pitch + col : -1;
+        }
+        const int qlo = max(0, s0 - c0), qhi = min(aw, s0 + sb - c0);
+        for (int q = qlo; q < qhi; ++q) {
+          const R wq = __shfl_sync(0xffffffffu, pw, q);
           const R qr = dr * wq, qi = di * wq;
-          CT* base = acc + (c0 + q - s0) * plane_elems + col;
-          if (rows_in) {   // the footprint's rows all fall in the tile (the common case)
-#pragma unroll
-            for (int i = 0; i < G; ++i) {
-              if (i < alpha) {
-                atomicAdd(&base[(ru + i) * pitch].x, qr * wu[i]);
-                atomicAdd(&base[(ru + i) * pitch].y, qi * wu[i]);
-              }
-            }
-          } else {
-#pragma unroll
-            for (int i = 0; i < G; ++i) {
-              const int row = ru + i;
-              if (i < alpha && row >= 0 && row < T) {
-                atomicAdd(&base[row * pitch].x, qr * wu[i]);
-                atomicAdd(&base[row * pitch].y, qi * wu[i]);
-              }
+          R* bre = acc + (c0 + q - s0) * plane_elems;
+          R* bim = acc_im + (c0 + q - s0) * plane_elems;
+  #pragma unroll
+          for (int k = 0; k < KR; ++k) {
+            if (off[k] >= 0) {
+              atomicAdd(bre + off[k], qr * cw[k]);
+              atomicAdd(bim + off[k], qi * cw[k]);
             }
           }
         }
@@ -547,8 +562,10 @@ k_grid_atomic(const Geom g, const __grid_constant__ Coef<R> coef, const IndexVie
   for (int e = threadIdx.x; e < sb * T * T; e += blockDim.x) {
     const int pl = e / (T * T), rem = e - pl * T * T;
     const int r = rem / T, c = rem - r * T;
-    planes[(int64_t)(s0 - b0 + pl) * pstride + (int64_t)(tu * T + r) * g.nv + tv * T + c] =
-        acc[pl * plane_elems + r * pitch + c];
+    CT o;
+    o.x = acc[pl * plane_elems + r * pitch + c];
+    o.y = acc_im[pl * plane_elems + r * pitch + c];
+    planes[(int64_t)(s0 - b0 + pl) * pstride + (int64_t)(tu * T + r) * g.nv + tv * T + c] = o;
   }
 }
 
@@ -590,6 +607,8 @@ template cudaError_t launch_weights<double>(const Geom&, const Coef<double>&,
 // ---------------------------------------------------------------------------------------
 constexpr size_t kDegridSmemBudget = 72 * 1024;
 constexpr size_t kGridSmemBudget = 110 * 1024;
+// 72 KB: three gridding CTAs per SM (with two, 110 KB, the 1e8-visibility FP32 gridding took
+// 244 ms instead of 197 ms: too few warps to hide the latency of the atomics' read-modify-write)
 constexpr size_t kGridAtomicSmemBudget = 72 * 1024;
 
 template <typename R>
@@ -648,7 +667,10 @@ template <typename R, int G>
 static cudaError_t grid_atomic_g(const Geom& g, const Coef<R>& coef, const IndexView<R>& ix,
                                  const typename C2<R>::T* vis, const R* wgt,
                                  typename C2<R>::T* planes, int b0, int nb, cudaStream_t s) {
-  const int pitch = g.tile + (sizeof(R) == 4 ? 8 : 0);
+  // row pitch = G (mod 32) words: the 32 lanes of an atomic add (G columns x 32 / G rows)
+  // fall in 32 different banks
+  int pitch = g.tile;
+  while (pitch % 32 != G % 32) ++pitch;
   const size_t per = (size_t)g.tile * pitch * sizeof(typename C2<R>::T);
   int bs = (int)std::max<size_t>(1, (kGridAtomicSmemBudget - coef_bytes<R>()) / per);
   bs = std::min(bs, nb);
