@@ -437,6 +437,12 @@ k_grid_owner(const Geom g, const __grid_constant__ Coef<R> coef, const IndexView
 // (rg > 0) and in w, and the warp exchanges them by shuffles.  Warps run concurrently, so cells
 // shared by overlapping footprints are combined by the atomics (summation order not fixed).
 // ---------------------------------------------------------------------------------------
+// Shared memory per gridding CTA, 54 KB: four gridding CTAs per SM (with the kernel held to 64 registers).  The kernel is
+// latency-bound (the atomics' read-modify-write); measured on the 1e8-visibility FP32 workload:
+// two CTAs per SM (110 KB) 244 ms, three (72 KB) 197-263 ms, four 175 ms
+constexpr size_t kGridAtomicSmemBudget = 54 * 1024;
+constexpr int kGridAtomicMinBlocks = 4;
+
 template <int G>
 struct AtomicLayout {
   static constexpr int kRowGroups = 32 / G;                      // rows handled at once
@@ -444,7 +450,7 @@ struct AtomicLayout {
 };
 
 template <typename R, int G>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, kGridAtomicMinBlocks)
 k_grid_atomic(const Geom g, const __grid_constant__ Coef<R> coef, const IndexView<R> ix,
               const typename C2<R>::T* __restrict__ vis, const R* __restrict__ wgt,
               typename C2<R>::T* __restrict__ planes, int b0, int nb, int bs, int pitch) {
@@ -531,7 +537,7 @@ k_grid_atomic(const Geom g, const __grid_constant__ Coef<R> coef, const IndexVie
         const bool colok = lj && col >= 0 && col < T;
         R cw[KR];
         int off[KR];
-  #pragma unroll
+#pragma unroll
         for (int k = 0; k < KR; ++k) {
           const int i = rg + k * RG;
           const R pu = __shfl_sync(0xffffffffu, puv, i < G ? i : 0);   // lane i holds u piece i
@@ -546,7 +552,7 @@ k_grid_atomic(const Geom g, const __grid_constant__ Coef<R> coef, const IndexVie
           const R qr = dr * wq, qi = di * wq;
           R* bre = acc + (c0 + q - s0) * plane_elems;
           R* bim = acc_im + (c0 + q - s0) * plane_elems;
-  #pragma unroll
+#pragma unroll
           for (int k = 0; k < KR; ++k) {
             if (off[k] >= 0) {
               atomicAdd(bre + off[k], qr * cw[k]);
@@ -607,9 +613,6 @@ template cudaError_t launch_weights<double>(const Geom&, const Coef<double>&,
 // ---------------------------------------------------------------------------------------
 constexpr size_t kDegridSmemBudget = 72 * 1024;
 constexpr size_t kGridSmemBudget = 110 * 1024;
-// 72 KB: three gridding CTAs per SM (with two, 110 KB, the 1e8-visibility FP32 gridding took
-// 244 ms instead of 197 ms: too few warps to hide the latency of the atomics' read-modify-write)
-constexpr size_t kGridAtomicSmemBudget = 72 * 1024;
 
 template <typename R>
 static size_t coef_bytes() { return (kMaxDeg + 1) * kMaxG * sizeof(R); }
