@@ -611,10 +611,12 @@ template cudaError_t launch_weights<double>(const Geom&, const Coef<double>&,
 // ---------------------------------------------------------------------------------------
 // launchers: sub-batch sizes from a shared-memory budget per CTA
 // ---------------------------------------------------------------------------------------
-// degridding CTA shared memory: 54 KB, four CTAs per SM (measured on the 1e8-visibility FP32
+// degridding CTA shared memory: FP32 54 KB, four CTAs per SM (measured on the 1e8-visibility
 // workload: 72 KB 71.9 ms, 54 KB 61.3 ms, 44 KB 66.8 ms -- fewer planes per CTA against more
-// warps to hide the staging loads)
-constexpr size_t kDegridSmemBudget = 54 * 1024;
+// warps to hide the staging loads); FP64 72 KB (FP64-pipe bound: more planes per CTA, fewer
+// visits per visibility)
+template <typename R>
+constexpr size_t degrid_smem_budget() { return sizeof(R) == 4 ? 54 * 1024 : 72 * 1024; }
 constexpr size_t kGridSmemBudget = 110 * 1024;
 
 template <typename R>
@@ -628,7 +630,7 @@ static size_t degrid_plane_bytes(const Geom& g) {
 
 template <typename R>
 int degrid_subbatch(const Geom& g) {
-  return (int)std::max<size_t>(1, (kDegridSmemBudget - coef_bytes<R>()) / degrid_plane_bytes<R>(g));
+  return (int)std::max<size_t>(1, (degrid_smem_budget<R>() - coef_bytes<R>()) / degrid_plane_bytes<R>(g));
 }
 
 template <typename R, int G>
