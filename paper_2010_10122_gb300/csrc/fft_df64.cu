@@ -19,94 +19,11 @@
 #include <cmath>
 #include <cstring>
 
+#include "df64.cuh"
 #include "host_math.h"
 #include "wgrid_internal.h"
 
 namespace wg {
-
-struct dd {
-  float h, l;
-};
-struct cdd {
-  dd r, i;
-};
-
-__device__ __forceinline__ dd dd_make(float h, float l) { dd x; x.h = h; x.l = l; return x; }
-
-// s + e = a + b exactly (Knuth)
-__device__ __forceinline__ dd two_sum(float a, float b) {
-  float s = __fadd_rn(a, b);
-  float bb = __fsub_rn(s, a);
-  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-  return dd_make(s, e);
-}
-// s + e = a + b exactly when |a| >= |b| (Dekker)
-__device__ __forceinline__ dd fast_two_sum(float a, float b) {
-  float s = __fadd_rn(a, b);
-  float e = __fsub_rn(b, __fsub_rn(s, a));
-  return dd_make(s, e);
-}
-__device__ __forceinline__ dd dd_add(dd a, dd b) {
-  dd s = two_sum(a.h, b.h);
-  float e = __fadd_rn(s.l, __fadd_rn(a.l, b.l));
-  return fast_two_sum(s.h, e);
-}
-__device__ __forceinline__ dd dd_neg(dd a) { return dd_make(-a.h, -a.l); }
-__device__ __forceinline__ dd dd_sub(dd a, dd b) { return dd_add(a, dd_neg(b)); }
-__device__ __forceinline__ dd dd_mul(dd a, dd b) {
-  float p = __fmul_rn(a.h, b.h);
-  float e = __fmaf_rn(a.h, b.h, -p);
-  e = __fmaf_rn(a.h, b.l, e);
-  e = __fmaf_rn(a.l, b.h, e);
-  return fast_two_sum(p, e);
-}
-
-__device__ __forceinline__ cdd c_add(cdd a, cdd b) { cdd c; c.r = dd_add(a.r, b.r); c.i = dd_add(a.i, b.i); return c; }
-__device__ __forceinline__ cdd c_sub(cdd a, cdd b) { cdd c; c.r = dd_sub(a.r, b.r); c.i = dd_sub(a.i, b.i); return c; }
-// x.h y.h + u.h v.h (sign: su = +1 or -1 for the second product) with the cross terms, as one
-// normalised pair: both leading products are split exactly (fma), summed exactly (two-sum),
-// and the small terms (product errors, cross products, low parts) are accumulated in float.
-// 19 FP32 operations instead of two products and a sum (25).
-__device__ __forceinline__ dd dd_dot2(dd x, dd y, dd u, dd v, float su) {
-  const float p1 = __fmul_rn(x.h, y.h);
-  const float e1 = __fmaf_rn(x.h, y.h, -p1);
-  const float uh = su * u.h, ul = su * u.l;
-  const float p2 = __fmul_rn(uh, v.h);
-  const float e2 = __fmaf_rn(uh, v.h, -p2);
-  dd s = two_sum(p1, p2);
-  float t = __fadd_rn(__fadd_rn(e1, e2), s.l);
-  t = __fmaf_rn(x.h, y.l, t);
-  t = __fmaf_rn(x.l, y.h, t);
-  t = __fmaf_rn(uh, v.l, t);
-  t = __fmaf_rn(ul, v.h, t);
-  return fast_two_sum(s.h, t);
-}
-__device__ __forceinline__ cdd c_mul(cdd a, cdd b) {
-  cdd c;
-  c.r = dd_dot2(a.r, b.r, a.i, b.i, -1.0f);
-  c.i = dd_dot2(a.r, b.i, a.i, b.r, 1.0f);
-  return c;
-}
-__device__ __forceinline__ cdd c_scale(cdd a, dd s) { cdd c; c.r = dd_mul(a.r, s); c.i = dd_mul(a.i, s); return c; }
-// multiply by -i (fwd = true) or +i
-__device__ __forceinline__ cdd c_mul_mi(cdd a, bool fwd) {
-  cdd c;
-  if (fwd) { c.r = a.i; c.i = dd_neg(a.r); }
-  else { c.r = dd_neg(a.i); c.i = a.r; }
-  return c;
-}
-
-__device__ __forceinline__ cdd load_cdd(const float4& v) {
-  cdd c; c.r = dd_make(v.x, v.y); c.i = dd_make(v.z, v.w); return c;
-}
-__device__ __forceinline__ float4 store_cdd(const cdd& c) { return make_float4(c.r.h, c.r.l, c.i.h, c.i.l); }
-
-__device__ __forceinline__ dd split_double(double x) {
-  float h = __double2float_rn(x);
-  float l = __double2float_rn(x - (double)h);
-  return dd_make(h, l);
-}
-__device__ __forceinline__ double join_double(dd x) { return (double)x.h + (double)x.l; }
 
 // df64 constants of the small DFT kernels
 struct DftConst {
@@ -254,7 +171,7 @@ __device__ __forceinline__ void stage(const float4* __restrict__ src, float4* __
 // plane * plane_elems + line * line_stride + i * elem_stride (complex elements).  The plane's
 // transformed lines are numbered 0 .. lines_per_plane - 1; those from `split` on are shifted
 // by `skip` (a pass over the first and last rows of a plane only, skipping the middle).
-// mode 0: load doubles, store df64; mode 1: load df64, store doubles.  Elements lhalf ..
+// mode 0: load doubles, store df64; mode 1: load df64, store doubles; mode 2: load and store df64.  Elements lhalf ..
 // n - lhalf - 1 are known zeros and not loaded, elements shalf .. n - shalf - 1 are not stored
 // (lhalf = shalf = n: everything).  Two n-element
 // shared-memory buffers (ping-pong); kAll adds the rare radices 2, 7 and 11, kept out of the
@@ -325,7 +242,7 @@ k_fft_lines(const __grid_constant__ FftLine L, void* __restrict__ data, int64_t 
     float4* t = src; src = dst; dst = t;
     Ns *= R;
   }
-  if (mode == 0) {
+  if (mode != 1) {
     float4* out = reinterpret_cast<float4*>(data) + base;
     for (int i = threadIdx.x; i < n; i += T)
       if (i < shalf || i >= n - shalf) out[i * elem_stride] = src[swizzle(i, swz)];
@@ -446,6 +363,9 @@ static cudaError_t launch_lines(const FftLine& L, double2* data, int64_t batch, 
 }
 
 // In-place transform of `batch` nu x nv complex128 planes; sign -1 forward, +1 inverse.
+// df64_planes: the planes on the grid side are double-float pairs (float4 per complex value:
+// re hi, re lo, im hi, im lo) instead of doubles -- the forward transform's output and the
+// inverse transform's input; the image side stays complex128.
 // keep_rows = keep_cols = 0: the full 2-D transform.  Otherwise only the image block -- the first
 // and last keep_rows/2 rows and keep_cols/2 columns of a plane -- matters:
 //  forward: it holds the only nonzero input, so the row pass runs over the image rows and
@@ -454,7 +374,7 @@ static cudaError_t launch_lines(const FftLine& L, double2* data, int64_t batch, 
 //  inverse: only it is read afterwards, so the column pass runs first and the row pass over the
 //    image rows, storing only their image columns (other cells are left undefined).
 cudaError_t df64_fft_exec(Df64Fft* f, double2* data, int64_t batch, int sign, cudaStream_t s,
-                          int64_t keep_rows, int64_t keep_cols) {
+                          int64_t keep_rows, int64_t keep_cols, bool df64_planes) {
   const int64_t plane = (int64_t)f->nu * f->nv;
   const int fwd = sign < 0 ? 1 : 0;
   const bool prune = keep_rows > 0 && keep_cols > 0;
@@ -471,10 +391,12 @@ cudaError_t df64_fft_exec(Df64Fft* f, double2* data, int64_t batch, int sign, cu
     // df64 -> doubles
     e = launch_lines(f->lv, data, batch, plane, nrows, f->nv, 1, 0, fwd, split, skip, ch, f->nv, s);
     if (e != cudaSuccess) return e;
-    return launch_lines(f->lu, data, batch, plane, f->nv, 1, f->nv, 1, fwd, f->nv, 0, rh, f->nu, s);
+    return launch_lines(f->lu, data, batch, plane, f->nv, 1, f->nv, df64_planes ? 2 : 1, fwd, f->nv,
+                        0, rh, f->nu, s);
   }
-  // pruned inverse: columns doubles -> df64, then the image rows df64 -> doubles
-  e = launch_lines(f->lu, data, batch, plane, f->nv, 1, f->nv, 0, fwd, f->nv, 0, f->nu, f->nu, s);
+  // pruned inverse: columns doubles (or df64) -> df64, then the image rows df64 -> doubles
+  e = launch_lines(f->lu, data, batch, plane, f->nv, 1, f->nv, df64_planes ? 2 : 0, fwd, f->nv, 0,
+                   f->nu, f->nu, s);
   if (e != cudaSuccess) return e;
   return launch_lines(f->lv, data, batch, plane, nrows, f->nv, 1, 1, fwd, split, skip, f->nv, ch, s);
 }

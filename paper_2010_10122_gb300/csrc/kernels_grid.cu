@@ -16,6 +16,7 @@
 //    separate zeroing pass; empty tiles write zeros).  Two accumulation schemes: shared-memory
 //    atomics (cheap in FP32) or warps that each own whole planes (no atomics, deterministic;
 //    used for FP64, where shared-memory double atomics occupy the FP64 pipe).
+#include "df64.cuh"
 #include "wgrid_internal.h"
 
 namespace wg {
@@ -179,6 +180,117 @@ k_degrid(const Geom g, const __grid_constant__ Coef<R> coef, const IndexView<R> 
       const int slot = sbid - c0 / bs;
       CT o; o.x = ar; o.y = ai;
       partial[(int64_t)slot * nvis_idx + vi] = o;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// degrid of double-float planes (FP64 plans with the double-float FFT)
+//
+// The same decomposition as k_degrid, on planes whose cells are double-float pairs (float4:
+// re hi, re lo, im hi, im lo): the tile + halo is staged as is, kernel values come as pairs
+// (the kernel-value table stores them split), and the footprint sum runs in pair arithmetic on
+// the FP32 pipes (dd_fma: 15 FP32 instructions for an FP64 FMA, which GB300 issues at 1/64 of
+// the FP32 rate).  Each lane sums its column over rows and planes, the lanes' sums are reduced
+// by shuffles in pair arithmetic, and the partial sum is stored in FP64 as in k_degrid.
+// ---------------------------------------------------------------------------------------
+// piece j of direction d of indexed visibility vi as a double-float pair
+__device__ __forceinline__ dd kernel_value_dd(const IndexView<double>& ix, const double* __restrict__ sc,
+                                              int deg, uint32_t vi, int d, int j, double z) {
+  if (ix.wts != nullptr) {
+    const float2 p = reinterpret_cast<const float2*>(ix.wts)[(int64_t)vi * (3 * kMaxG) + d * kMaxG + j];
+    return dd_make(p.x, p.y);
+  }
+  return split_double(horner(sc, deg, j, z));
+}
+
+__device__ __forceinline__ dd shfl_dd(dd x, int src, int width) {
+  return dd_make(__shfl_sync(0xffffffffu, x.h, src, width), __shfl_sync(0xffffffffu, x.l, src, width));
+}
+
+template <int G>
+__global__ void __launch_bounds__(kThreads)
+k_degrid_dd(const Geom g, const __grid_constant__ Coef<double> coef, const IndexView<double> ix,
+            const double2* __restrict__ planes, int b0, int nb, int bs,
+            double2* __restrict__ partial, int64_t nvis_idx) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  double* sc = reinterpret_cast<double*>(smem);
+  double2* st = reinterpret_cast<double2*>(smem + (kMaxDeg + 1) * kMaxG * sizeof(double));
+  const int T = g.tile, alpha = g.alpha, aw = g.alpha_w;
+  const int TH = T + alpha - 1;
+  const int t = blockIdx.x;
+  const int tu = t / g.ntv, tv = t - tu * g.ntv;
+  const int s0 = b0 + blockIdx.y * bs;
+  const int sb = min(bs, b0 + nb - s0);
+  const int sbid = s0 / bs;                       // global sub-batch id (s0 is a multiple of bs)
+  const uint32_t* offt = ix.off + (int64_t)t * g.nw;
+  const uint32_t lo = offt[max(0, s0 - aw + 1)], hi = offt[min(g.nw, s0 + sb)];
+  if (lo == hi) return;                           // no visibility of this tile meets these planes
+  for (int i = threadIdx.x; i < (g.deg + 1) * kMaxG; i += blockDim.x) sc[i] = coef.c[i];
+  const int64_t pstride = (int64_t)g.nu * g.nv;
+  for (int pl = 0; pl < sb; ++pl) {
+    const int p = s0 + pl;
+    if (offt[max(0, p - aw + 1)] == offt[min(p + 1, g.nw)]) continue;  // plane unused here
+    const double2* src = planes + (int64_t)(p - b0) * pstride;
+    double2* dst = st + pl * TH * TH;
+    for (int e = threadIdx.x; e < TH * TH; e += blockDim.x) {
+      int r = e / TH, c = e - r * TH;
+      int gu = tu * T + r; if (gu >= g.nu) gu -= g.nu;
+      int gv = tv * T + c; if (gv >= g.nv) gv -= g.nv;
+      dst[e] = src[(int64_t)gu * g.nv + gv];       // 16 bytes, copied as they are
+    }
+  }
+  __syncthreads();
+  const int j = threadIdx.x & (G - 1);
+  const int grp = threadIdx.x / G, ngrp = blockDim.x / G;
+  const dd zero = dd_make(0.f, 0.f);
+  for (uint32_t v0 = lo + (threadIdx.x >> 5) * (32 / G); v0 < hi; v0 += ngrp) {
+    const uint32_t vi = v0 + (grp % (32 / G));
+    const bool act = vi < hi;
+    uint32_t mt = 0;
+    Z4<double> zz;
+    zz.u = zz.v = zz.w = zz.pad = 0.0;
+    if (act) { mt = ix.meta[vi]; if (ix.wts == nullptr) zz = ix.z[vi]; }
+    const int du = mt & 255, dv = (mt >> 8) & 255, c0 = (int)(mt >> 16);
+    const bool lj = act && j < alpha;
+    const dd pu = lj ? kernel_value_dd(ix, sc, g.deg, vi, 0, j, zz.u) : zero;
+    const dd pv = lj ? kernel_value_dd(ix, sc, g.deg, vi, 1, j, zz.v) : zero;
+    const dd pw = g.do_w ? (lj ? kernel_value_dd(ix, sc, g.deg, vi, 2, j, zz.w) : zero)
+                         : (j == 0 ? dd_make(1.f, 0.f) : zero);
+    dd wu[G];
+#pragma unroll
+    for (int i = 0; i < G; ++i) wu[i] = shfl_dd(pu, i, G);
+    const int qlo = act ? max(0, s0 - c0) : G, qhi = act ? min(aw, s0 + sb - c0) : 0;
+    const int wlo = __reduce_min_sync(0xffffffffu, (unsigned)qlo);
+    const int whi = __reduce_max_sync(0xffffffffu, (unsigned)qhi);
+    dd ar = zero, ai = zero;
+    for (int q = wlo; q < whi; ++q) {
+      const dd wq = shfl_dd(pw, q, G);
+      if (lj && q >= qlo && q < qhi) {
+        const float4* row = reinterpret_cast<const float4*>(st + (c0 + q - s0) * TH * TH + du * TH + dv + j);
+        dd sr = zero, si = zero;
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+          if (i < alpha) {
+            const float4 gv = row[i * TH];
+            sr = dd_fma(wu[i], dd_make(gv.x, gv.y), sr);
+            si = dd_fma(wu[i], dd_make(gv.z, gv.w), si);
+          }
+        }
+        ar = dd_fma(wq, sr, ar);
+        ai = dd_fma(wq, si, ai);
+      }
+    }
+    ar = dd_mul(ar, pv);
+    ai = dd_mul(ai, pv);
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+      ar = dd_add(ar, dd_make(__shfl_xor_sync(0xffffffffu, ar.h, o, G), __shfl_xor_sync(0xffffffffu, ar.l, o, G)));
+      ai = dd_add(ai, dd_make(__shfl_xor_sync(0xffffffffu, ai.h, o, G), __shfl_xor_sync(0xffffffffu, ai.l, o, G)));
+    }
+    if (act && j == 0) {
+      const int slot = sbid - c0 / bs;
+      partial[(int64_t)slot * nvis_idx + vi] = make_double2(join_double(ar), join_double(ai));
     }
   }
 }
@@ -427,6 +539,171 @@ k_grid_owner(const Geom g, const __grid_constant__ Coef<R> coef, const IndexView
 }
 
 // ---------------------------------------------------------------------------------------
+// grid of double-float planes (FP64 plans with the double-float FFT): the plane-owner scheme
+// of k_grid_owner with the staged 2-D weights, the plane-weighted data and the accumulators as
+// double-float pairs, updated in pair arithmetic on the FP32 pipes (dd_fma), and the planes
+// written as pairs (float4 per cell) for the double-float FFT.
+// ---------------------------------------------------------------------------------------
+template <int G>
+struct GridStageDD {
+  // kernel values in u and v as pairs (the 2-D weight of a cell, one pair product, is formed
+  // where it is used: 7 FP32 instructions, cheaper than staging G^2 weights), and the data
+  // times the w kernel value of plane q (re hi, re lo, im hi, im lo)
+  static constexpr int kChunk = 48;
+  float2 wu[kChunk][G];
+  float2 wv[kChunk][G];
+  float4 dq[kChunk][G];
+  int ru[kChunk], rv[kChunk], c0[kChunk];
+};
+
+template <int G, int MC>
+__device__ __forceinline__ void owner_add_dd(const GridStageDD<G>* __restrict__ stg, int v,
+                                             const OwnerFootprint& fp, int lane, int T, int pitch,
+                                             int p1, int phi, int qoff, float4* __restrict__ acc,
+                                             int plane_elems) {
+  const float rw = 1.0f / (float)fp.w;
+  const int dummy = (lane >> 1) * pitch + T + (lane & 1);
+  dd wt[MC];
+  int off[MC];
+#pragma unroll
+  for (int m = 0; m < MC; ++m) {
+    const int c = lane + 32 * m;
+    // c = ii * w + jj; exact in float (see owner_add)
+    const int ii = (int)(((float)c + 0.5f) * rw), jj = c - ii * fp.w;
+    const bool ok = c < fp.cells;
+    const int i = fp.i0 + (ok ? ii : 0), j = fp.j0 + (ok ? jj : 0);
+    const float2 a = stg->wu[v][i], b = stg->wv[v][j];
+    wt[m] = ok ? dd_mul(dd_make(a.x, a.y), dd_make(b.x, b.y)) : dd_make(0.f, 0.f);
+    off[m] = ok ? (fp.ru + i) * pitch + fp.rv + j : dummy;
+  }
+  for (int pl = p1; pl < phi; pl += kOwnerWarps) {
+    const float4 q = stg->dq[v][pl + qoff];
+    float4* base = acc + pl * plane_elems;
+#pragma unroll
+    for (int m = 0; m < MC; ++m) {
+      float4 a = base[off[m]];
+      const dd re = dd_fma(dd_make(q.x, q.y), wt[m], dd_make(a.x, a.y));
+      const dd im = dd_fma(dd_make(q.z, q.w), wt[m], dd_make(a.z, a.w));
+      base[off[m]] = make_float4(re.h, re.l, im.h, im.l);
+    }
+  }
+}
+
+template <int G>
+__global__ void __launch_bounds__(kOwnerThreads)
+k_grid_owner_dd(const Geom g, const __grid_constant__ Coef<double> coef, const IndexView<double> ix,
+                const double2* __restrict__ vis, const double* __restrict__ wgt,
+                double2* __restrict__ planes, int b0, int nb, int bs, int pitch) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  double* sc = reinterpret_cast<double*>(smem);
+  using Stage = GridStageDD<G>;
+  constexpr int kChunk = Stage::kChunk;
+  Stage* stg = reinterpret_cast<Stage*>(smem + (kMaxDeg + 1) * kMaxG * sizeof(double));
+  float4* acc = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(stg) + sizeof(Stage));
+  const int T = g.tile, alpha = g.alpha, aw = g.alpha_w;
+  const int t = blockIdx.x;
+  const int tu = t / g.ntv, tv = t - tu * g.ntv;
+  const int s0 = b0 + blockIdx.y * bs;
+  const int sb = min(bs, b0 + nb - s0);
+  const int plane_elems = T * pitch;
+  for (int i = threadIdx.x; i < (g.deg + 1) * kMaxG; i += blockDim.x) sc[i] = coef.c[i];
+  for (int e = threadIdx.x; e < sb * plane_elems; e += blockDim.x) acc[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j1 = threadIdx.x & (G - 1), grp = threadIdx.x / G, ngrp = blockDim.x / G;
+  const unsigned gmask = group_mask<G>();
+  const dd zero = dd_make(0.f, 0.f);
+  __syncthreads();   // coefficients staged
+
+  for (int src = 0; src < 4; ++src) {
+    const int ou = (src & 1) ? -1 : 0, ov = (src & 2) ? -1 : 0;
+    int stu = tu + ou; if (stu < 0) stu += g.ntu;
+    int stv = tv + ov; if (stv < 0) stv += g.ntv;
+    const uint32_t* offs = ix.off + ((int64_t)stu * g.ntv + stv) * g.nw;
+    const uint32_t lo = offs[max(0, s0 - aw + 1)], hi = offs[min(g.nw, s0 + sb)];
+    for (uint32_t cs = lo; cs < hi; cs += kChunk) {
+      const int nch = (int)min((uint32_t)kChunk, hi - cs);
+      __syncthreads();  // previous chunk consumed (and accumulators zeroed)
+      // ---- phase 1: kernel values and plane-weighted data of the chunk, as pairs ----
+      for (int v = grp; v < nch; v += ngrp) {
+        const uint32_t vi = cs + v;
+        const uint32_t mt = ix.meta[vi];
+        const int ru = (int)(mt & 255) + ou * T, rv = (int)((mt >> 8) & 255) + ov * T;
+        const bool hit = (ru + alpha > 0) && (rv + alpha > 0);
+        if (j1 == 0) {
+          stg->ru[v] = ru; stg->rv[v] = rv;
+          stg->c0[v] = hit ? (int)(mt >> 16) : -(1 << 20);
+        }
+        if (!hit) continue;   // uniform within the group
+        Z4<double> zz;
+        zz.u = zz.v = zz.w = zz.pad = 0.0;
+        if (ix.wts == nullptr) zz = ix.z[vi];
+        const bool lj = j1 < alpha;
+        const dd pu = lj ? kernel_value_dd(ix, sc, g.deg, vi, 0, j1, zz.u) : zero;
+        const dd pv = lj ? kernel_value_dd(ix, sc, g.deg, vi, 1, j1, zz.v) : zero;
+        stg->wu[v][j1] = make_float2(pu.h, pu.l);
+        stg->wv[v][j1] = make_float2(pv.h, pv.l);
+        const dd wwj = g.do_w ? (lj ? kernel_value_dd(ix, sc, g.deg, vi, 2, j1, zz.w) : zero)
+                              : (j1 == 0 ? dd_make(1.f, 0.f) : zero);
+        dd dr = zero, di = zero;
+        if (j1 == 0) {
+          const uint32_t id = ix.idx[vi];
+          const int64_t k = id & ~kFoldBit;
+          const double2 d = vis[k];
+          double xr = d.x, xi = d.y;
+          if (wgt != nullptr) { const double w = wgt[k]; xr *= w; xi *= w; }
+          if (id & kFoldBit) xi = -xi;      // grid conj(d) at the folded coordinates
+          if (ix.ph != nullptr) {           // times conj(exp(2 pi i w nshift))
+            const double2 ph = ix.ph[vi];
+            const double r = xr * ph.x + xi * ph.y;
+            xi = xi * ph.x - xr * ph.y;
+            xr = r;
+          }
+          dr = split_double(xr);
+          di = split_double(xi);
+        }
+        dr = dd_make(__shfl_sync(gmask, dr.h, 0, G), __shfl_sync(gmask, dr.l, 0, G));
+        di = dd_make(__shfl_sync(gmask, di.h, 0, G), __shfl_sync(gmask, di.l, 0, G));
+        const dd qr = dd_mul(dr, wwj), qi = dd_mul(di, wwj);
+        stg->dq[v][j1] = make_float4(qr.h, qr.l, qi.h, qi.l);
+      }
+      __syncthreads();
+      // ---- phase 2: each warp adds the chunk into its own planes ----
+      for (int v = 0; v < nch; ++v) {
+        const int c0 = stg->c0[v];
+        if (c0 < -1000) continue;
+        const int plo = max(0, c0 - s0), phi = min(sb, c0 - s0 + aw);
+        const int p1 = plo + ((warp - plo) & (kOwnerWarps - 1));
+        if (p1 >= phi) continue;
+        const int ru = stg->ru[v], rv = stg->rv[v];
+        const int i0 = max(0, -ru), i1 = min(alpha, T - ru);
+        const int j0 = max(0, -rv), j1c = min(alpha, T - rv);
+        const int w = j1c - j0, cells = (i1 - i0) * w;
+        const OwnerFootprint fp{i0, j0, w, cells, ru, rv};
+        switch ((cells + 31) >> 5) {
+          case 1: owner_add_dd<G, 1>(stg, v, fp, lane, T, pitch, p1, phi, s0 - c0, acc, plane_elems); break;
+          case 2: owner_add_dd<G, 2>(stg, v, fp, lane, T, pitch, p1, phi, s0 - c0, acc, plane_elems); break;
+          case 3: owner_add_dd<G, (G > 8 ? 3 : 1)>(stg, v, fp, lane, T, pitch, p1, phi, s0 - c0, acc, plane_elems); break;
+          case 4: owner_add_dd<G, (G > 8 ? 4 : 1)>(stg, v, fp, lane, T, pitch, p1, phi, s0 - c0, acc, plane_elems); break;
+          case 5: owner_add_dd<G, (G > 8 ? 5 : 1)>(stg, v, fp, lane, T, pitch, p1, phi, s0 - c0, acc, plane_elems); break;
+          case 6: owner_add_dd<G, (G > 8 ? 6 : 1)>(stg, v, fp, lane, T, pitch, p1, phi, s0 - c0, acc, plane_elems); break;
+          case 7: owner_add_dd<G, (G > 8 ? 7 : 1)>(stg, v, fp, lane, T, pitch, p1, phi, s0 - c0, acc, plane_elems); break;
+          default: owner_add_dd<G, (G > 8 ? 8 : 1)>(stg, v, fp, lane, T, pitch, p1, phi, s0 - c0, acc, plane_elems); break;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  const int64_t pstride = (int64_t)g.nu * g.nv;
+  float4* out = reinterpret_cast<float4*>(planes);
+  for (int e = threadIdx.x; e < sb * T * T; e += blockDim.x) {
+    const int pl = e / (T * T), rem = e - pl * T * T;
+    const int r = rem / T, c = rem - r * T;
+    out[(int64_t)(s0 - b0 + pl) * pstride + (int64_t)(tu * T + r) * g.nv + tv * T + c] =
+        acc[pl * plane_elems + r * pitch + c];
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // grid, shared-atomic variant (default for FP32)
 //
 // CTA = (uv tile, sub-batch of planes), owning the T x T cells of those planes as separate real
@@ -591,7 +868,13 @@ __global__ void k_weights(const Geom g, const __grid_constant__ Coef<R> coef, co
   const Z4<R> zz = ix.z[pos];
   R v = (R)0;
   if (j < g.alpha) v = horner(sc, g.deg, j, d == 0 ? zz.u : (d == 1 ? zz.v : zz.w));
-  wts[e] = v;
+  if (sizeof(R) == 8 && g.df64_planes) {
+    // the pair-arithmetic kernels read the value as a double-float pair (same 8 bytes)
+    const dd p = split_double((double)v);
+    reinterpret_cast<float2*>(wts)[e] = make_float2(p.h, p.l);
+  } else {
+    wts[e] = v;
+  }
 }
 
 template <typename R>
@@ -638,11 +921,20 @@ static cudaError_t degrid_g(const Geom& g, const Coef<R>& coef, const IndexView<
                             const typename C2<R>::T* planes, int b0, int nb, int bs,
                             typename C2<R>::T* partial, int64_t nvis_idx, cudaStream_t s) {
   size_t smem = coef_bytes<R>() + (size_t)std::min(bs, nb) * degrid_plane_bytes<R>(g);
+  int64_t ntiles = (int64_t)g.ntu * g.ntv;
+  dim3 grid((unsigned)ntiles, (unsigned)((nb + bs - 1) / bs));
+  if constexpr (sizeof(R) == 8) {
+    if (g.df64_planes) {
+      cudaError_t e = cudaFuncSetAttribute(k_degrid_dd<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+      if (e != cudaSuccess) return e;
+      k_degrid_dd<G><<<grid, kThreads, smem, s>>>(g, coef, ix, planes, b0, nb, bs, partial, nvis_idx);
+      return cudaGetLastError();
+    }
+  }
   cudaError_t e = cudaFuncSetAttribute(k_degrid<R, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  int64_t ntiles = (int64_t)g.ntu * g.ntv;
-  dim3 grid((unsigned)ntiles, (unsigned)((nb + bs - 1) / bs));
   k_degrid<R, G><<<grid, kThreads, smem, s>>>(g, coef, ix, planes, b0, nb, bs, partial, nvis_idx);
   return cudaGetLastError();
 }
@@ -656,17 +948,27 @@ static cudaError_t grid_owner_g(const Geom& g, const Coef<R>& coef, const IndexV
   // cell for idle updates
   const int pitch = g.tile + 2;
   const size_t per = (size_t)g.tile * pitch * sizeof(typename C2<R>::T);
-  const size_t fixed = coef_bytes<R>() + sizeof(GridStage<R, G>);
+  const size_t stage = (sizeof(R) == 8 && g.df64_planes) ? sizeof(GridStageDD<G>) : sizeof(GridStage<R, G>);
+  const size_t fixed = coef_bytes<R>() + stage;
   const int nwarps = kOwnerWarps;
   int bs = (int)std::max<size_t>(1, (kGridSmemBudget - fixed) / per);
   if (bs > nwarps) bs -= bs % nwarps;  // equal planes per warp
   bs = std::min(bs, nb);
   size_t smem = fixed + (size_t)bs * per;
+  int64_t ntiles = (int64_t)g.ntu * g.ntv;
+  dim3 grid((unsigned)ntiles, (unsigned)((nb + bs - 1) / bs));
+  if constexpr (sizeof(R) == 8) {
+    if (g.df64_planes) {
+      cudaError_t e = cudaFuncSetAttribute(k_grid_owner_dd<G>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      k_grid_owner_dd<G><<<grid, kOwnerThreads, smem, s>>>(g, coef, ix, vis, wgt, planes, b0, nb, bs, pitch);
+      return cudaGetLastError();
+    }
+  }
   cudaError_t e = cudaFuncSetAttribute(k_grid_owner<R, G>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  int64_t ntiles = (int64_t)g.ntu * g.ntv;
-  dim3 grid((unsigned)ntiles, (unsigned)((nb + bs - 1) / bs));
   k_grid_owner<R, G><<<grid, kOwnerThreads, smem, s>>>(g, coef, ix, vis, wgt, planes, b0, nb, bs, pitch);
   return cudaGetLastError();
 }
@@ -696,7 +998,8 @@ template <typename R, int G>
 static cudaError_t grid_g(const Geom& g, const Coef<R>& coef, const IndexView<R>& ix,
                           const typename C2<R>::T* vis, const R* wgt,
                           typename C2<R>::T* planes, int b0, int nb, cudaStream_t s) {
-  const bool owner = g.grid_variant == 2 || (g.grid_variant == 0 && sizeof(R) == 8);
+  // double-float planes are written by the plane-owner kernel only
+  const bool owner = g.grid_variant == 2 || (g.grid_variant == 0 && sizeof(R) == 8) || g.df64_planes;
   if (owner) return grid_owner_g<R, G>(g, coef, ix, vis, wgt, planes, b0, nb, s);
   return grid_atomic_g<R, G>(g, coef, ix, vis, wgt, planes, b0, nb, s);
 }

@@ -428,6 +428,9 @@ int wg_plan_create(const double* uvw, const double* freq, int64_t nrows, int64_t
   // plane FFTs: the kind the planner chose (FP64: pruned cuFFT Z2Z or the double-float FFT,
   // whichever is cheaper with its rounding inside epsilon)
   const bool use_df64 = pp.fft_kind == kFftDf64;
+  // with the double-float FFT the uv planes stay double-float pairs between the (de)gridding
+  // kernels and the transform, and the (de)gridding arithmetic runs in pair arithmetic too
+  g.df64_planes = use_df64 && precision == WG_F64 ? 1 : 0;
   if (use_df64 && !df64_fft_supported(pp.nu, pp.nv))
     return fail(set_error(WG_ERR_INTERNAL, "double-float FFT does not support %lld x %lld",
                           (long long)pp.nu, (long long)pp.nv));
@@ -588,7 +591,7 @@ static int run_fft(wg_plan* p, int64_t nb, void* data, void* work, int dir, cuda
     // the image occupies the first and last nx/2 rows and ny/2 columns of a plane: degrid's
     // input is zero elsewhere (and not written by the screen) and grid reads only that block
     cudaError_t e = df64_fft_exec(p->dfft, (double2*)data, nb, dir == CUFFT_FORWARD ? -1 : 1, s,
-                                  p->g.nx, p->g.ny);
+                                  p->g.nx, p->g.ny, p->g.df64_planes != 0);
     if (e != cudaSuccess) return set_error(WG_ERR_CUDA, "double-float FFT: %s", cudaGetErrorString(e));
     return WG_OK;
   }

@@ -39,6 +39,8 @@ struct Geom {
   double w0, dw, nshift;
   double w0_dw;         // w0 / dw
   int grid_variant;     // 0 automatic, 1 shared atomics, 2 plane-owner warps
+  int df64_planes;      // FP64 plans with the double-float FFT: the uv planes hold double-float
+                        // pairs (float4 per cell) and (de)gridding runs in pair arithmetic
 };
 
 // Kernel polynomial coefficients, layout [d][G] so lane j reads c[d * kMaxG + j].
@@ -73,7 +75,7 @@ bool df64_fft_supported(int64_t nu, int64_t nv);
 cudaError_t df64_fft_create(int64_t nu, int64_t nv, Df64Fft** out);
 void df64_fft_destroy(Df64Fft* f);
 cudaError_t df64_fft_exec(Df64Fft* f, double2* data, int64_t batch, int sign, cudaStream_t s,
-                          int64_t keep_rows = 0, int64_t keep_cols = 0);
+                          int64_t keep_rows = 0, int64_t keep_cols = 0, bool df64_planes = false);
 
 // ---- index kernels (kernels_index.cu) ------------------------------------------------
 cudaError_t launch_extent(const double* uvw, int64_t nrows, unsigned long long* ext4,
