@@ -408,7 +408,9 @@ static double plan_cost(int prec, int kind, int64_t nu, int64_t nv, int64_t nw, 
   double cells = (double)nu * nv;
   double k_cell = prec ? 3.0e-12 : 2.5e-12;   // s per plane cell (screen / (de)grid traffic)
   double k_pix = prec ? 6.0e-11 : 1.8e-12;    // s per image pixel per plane (screen phase)
-  double k_vis = prec ? 1.05e-11 : 3.6e-12;   // s per visibility per alpha^2 x lanes
+  // s per visibility per alpha^2 x lanes; FP64 plans with the double-float FFT (de)grid in pair
+  // arithmetic on the FP32 pipes, about twice as fast as FP64 arithmetic
+  double k_vis = prec ? (kind == kFftDf64 ? 5.0e-12 : 1.05e-11) : 3.6e-12;
   const int G = alpha <= 4 ? 4 : (alpha <= 8 ? 8 : 16);
   const double lanes = prec ? 0.5 * (G + alpha) : (double)G;
   return nw * (1e-3 * fft_ms(nu, nv, kind, prec, nx) + cells * k_cell + (double)npix * k_pix) +
