@@ -367,12 +367,14 @@ static cudaError_t launch_lines(const FftLine& L, double2* data, int64_t batch, 
 // re hi, re lo, im hi, im lo) instead of doubles -- the forward transform's output and the
 // inverse transform's input; the image side stays complex128.
 // keep_rows = keep_cols = 0: the full 2-D transform.  Otherwise only the image block -- the first
-// and last keep_rows/2 rows and keep_cols/2 columns of a plane -- matters:
-//  forward: it holds the only nonzero input, so the row pass runs over the image rows and
-//    loads only their image columns, and the column pass loads only the image rows (the rest
-//    is zero and never read, so the caller need not write it);
-//  inverse: only it is read afterwards, so the column pass runs first and the row pass over the
-//    image rows, storing only their image columns (other cells are left undefined).
+// and last keep_rows/2 rows and keep_cols/2 columns of a plane -- matters, and the column pass
+// (strided, the slower pass per line) runs over the image columns only:
+//  forward: the image block holds the only nonzero input: the column pass over the image
+//    columns loads only their image rows, then the row pass over all rows loads only the image
+//    columns (the rest is zero and never read, so the caller need not write it);
+//  inverse: only the image block is read afterwards: the row pass over all rows stores only the
+//    image columns, then the column pass over those columns stores only the image rows (other
+//    cells are left undefined).
 cudaError_t df64_fft_exec(Df64Fft* f, double2* data, int64_t batch, int sign, cudaStream_t s,
                           int64_t keep_rows, int64_t keep_cols, bool df64_planes) {
   const int64_t plane = (int64_t)f->nu * f->nv;
@@ -380,25 +382,33 @@ cudaError_t df64_fft_exec(Df64Fft* f, double2* data, int64_t batch, int sign, cu
   const bool prune = keep_rows > 0 && keep_cols > 0;
   if (prune && ((keep_rows & 1) || (keep_cols & 1) || keep_rows > f->nu || keep_cols > f->nv))
     return cudaErrorInvalidValue;
-  const int rh = prune ? (int)(keep_rows / 2) : f->nu;   // image half-extent along u (rows)
-  const int ch = prune ? (int)(keep_cols / 2) : f->nv;   // along v (columns)
-  const int nrows = prune ? 2 * rh : f->nu;
-  const int skip = f->nu - nrows;
-  const int split = prune ? rh : f->nu;
   cudaError_t e;
-  if (!prune || fwd) {
-    // rows (length nv, contiguous): doubles -> df64; then columns (length nu, stride nv):
-    // df64 -> doubles
-    e = launch_lines(f->lv, data, batch, plane, nrows, f->nv, 1, 0, fwd, split, skip, ch, f->nv, s);
+  if (!prune) {
+    // rows (length nv, contiguous): doubles (pairs: inverse of pair planes) -> df64; then
+    // columns (length nu, stride nv): df64 -> doubles (pairs: forward to pair planes)
+    e = launch_lines(f->lv, data, batch, plane, f->nu, f->nv, 1, !fwd && df64_planes ? 2 : 0, fwd,
+                     f->nu, 0, f->nv, f->nv, s);
     if (e != cudaSuccess) return e;
-    return launch_lines(f->lu, data, batch, plane, f->nv, 1, f->nv, df64_planes ? 2 : 1, fwd, f->nv,
-                        0, rh, f->nu, s);
+    return launch_lines(f->lu, data, batch, plane, f->nv, 1, f->nv, fwd && df64_planes ? 2 : 1, fwd,
+                        f->nv, 0, f->nu, f->nu, s);
   }
-  // pruned inverse: columns doubles (or df64) -> df64, then the image rows df64 -> doubles
-  e = launch_lines(f->lu, data, batch, plane, f->nv, 1, f->nv, df64_planes ? 2 : 0, fwd, f->nv, 0,
-                   f->nu, f->nu, s);
+  const int rh = (int)(keep_rows / 2);   // image half-extent along u (rows)
+  const int ch = (int)(keep_cols / 2);   // along v (columns)
+  const int ncols = 2 * ch, cskip = f->nv - ncols;   // image columns: [0, ch) and [nv - ch, nv)
+  if (fwd) {
+    // image columns (length nu, stride nv), image rows loaded: doubles -> df64; then all rows
+    // (length nv), image columns loaded: df64 -> pairs (or doubles)
+    e = launch_lines(f->lu, data, batch, plane, ncols, 1, f->nv, 0, fwd, ch, cskip, rh, f->nu, s);
+    if (e != cudaSuccess) return e;
+    return launch_lines(f->lv, data, batch, plane, f->nu, f->nv, 1, df64_planes ? 2 : 1, fwd, f->nu,
+                        0, ch, f->nv, s);
+  }
+  // inverse: all rows, image columns stored: pairs (or doubles) -> df64; then the image columns,
+  // image rows stored: df64 -> doubles
+  e = launch_lines(f->lv, data, batch, plane, f->nu, f->nv, 1, df64_planes ? 2 : 0, fwd, f->nu, 0,
+                   f->nv, ch, s);
   if (e != cudaSuccess) return e;
-  return launch_lines(f->lv, data, batch, plane, nrows, f->nv, 1, 1, fwd, split, skip, f->nv, ch, s);
+  return launch_lines(f->lu, data, batch, plane, ncols, 1, f->nv, 1, fwd, ch, cskip, f->nu, rh, s);
 }
 
 }  // namespace wg
