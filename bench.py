@@ -261,13 +261,14 @@ DF64_DRAM_PER_ALGORITHMIC_BYTE = 30.8 / 32.0
 
 
 def df64_fft_bytes(nx, ny, nu, nv, direction):
-    """Algorithmic bytes of one plane's double-float FFT in the library's pruned form: degrid
-    (forward) -- row pass over the nx image rows loading their ny image cells and storing nv,
-    column pass over nv columns loading the nx image rows and storing nu; grid (inverse) --
-    column pass over all nu x nv cells, row pass over the nx image rows storing ny."""
+    """Algorithmic bytes of one plane's double-float FFT in the library's pruned form (16 B per
+    cell read or written): degrid (forward) -- column pass over the ny image columns loading
+    their nx image rows and storing nu, row pass over all nu rows loading their ny image cells
+    and storing nv; grid (inverse) -- row pass over all nu x nv cells storing the ny image
+    columns, column pass over those loading nu and storing the nx image rows."""
     if direction == "degrid":
-        return 16 * (nx * ny + nx * nv) + 16 * (nv * nx + nv * nu)
-    return 16 * (2 * nu * nv) + 16 * (nx * nv + nx * ny)
+        return 16 * (nx * ny + nu * ny) + 16 * (nu * ny + nu * nv)
+    return 16 * (nu * nv + nu * ny) + 16 * (nu * ny + nx * ny)
 
 
 def run_sweep(args):
@@ -535,9 +536,9 @@ def main():
     roof = None
     if stage_d == "fft":
         # double-float plane FFT: FP32-ALU (issue) bound; work = its FP32 arithmetic
-        # instructions; one pass over the nx image rows (length nv), one over all nv columns
+        # instructions; one pass over the ny image columns (length nu), one over all nu rows
         nu, nv, nw = info_d["nu"], info_d["nv"], info_d["nw"]
-        ops = nw * (obs.npix_x * df64_line_ops(nv) + nv * df64_line_ops(nu))
+        ops = nw * (obs.npix_y * df64_line_ops(nu) + nu * df64_line_ops(nv))
         peak = 152 * 128 * 2.07e9   # SMs x FP32 lanes x max SM clock, one instruction per lane
         ach = ops / (stage_ms[dom] * 1e-3)
         abytes = nw * df64_fft_bytes(obs.npix_x, obs.npix_y, nu, nv, dir_d)
