@@ -539,6 +539,40 @@ k_grid_owner(const Geom g, const __grid_constant__ Coef<R> coef, const IndexView
 }
 
 // ---------------------------------------------------------------------------------------
+// per-call visibility data for the pair-arithmetic gridding: position pos of the index gets
+// wgt_k * d_k, conjugated where the visibility was folded (Hermitian symmetry), times
+// conj(e^{2 pi i w nshift}) (the w reference shift), as double-float pairs -- the FP64 work that
+// the gridding kernel would otherwise repeat on every (tile, sub-batch) visit
+// ---------------------------------------------------------------------------------------
+__global__ void k_grid_vis_dd(const IndexView<double> ix, const double2* __restrict__ vis,
+                              const double* __restrict__ wgt, int64_t nvis_idx,
+                              float4* __restrict__ out) {
+  const int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (pos >= nvis_idx) return;
+  const uint32_t id = ix.idx[pos];
+  const int64_t k = id & ~kFoldBit;
+  const double2 d = vis[k];
+  double xr = d.x, xi = d.y;
+  if (wgt != nullptr) { const double w = wgt[k]; xr *= w; xi *= w; }
+  if (id & kFoldBit) xi = -xi;      // grid conj(d) at the folded coordinates
+  if (ix.ph != nullptr) {           // times conj(exp(2 pi i w nshift))
+    const double2 ph = ix.ph[pos];
+    const double r = xr * ph.x + xi * ph.y;
+    xi = xi * ph.x - xr * ph.y;
+    xr = r;
+  }
+  const dd a = split_double(xr), b = split_double(xi);
+  out[pos] = make_float4(a.h, a.l, b.h, b.l);
+}
+
+cudaError_t launch_grid_vis_dd(const IndexView<double>& ix, const double2* vis, const double* wgt,
+                               int64_t nvis_idx, float4* out, cudaStream_t s) {
+  if (nvis_idx == 0) return cudaSuccess;
+  k_grid_vis_dd<<<(unsigned)((nvis_idx + 255) / 256), 256, 0, s>>>(ix, vis, wgt, nvis_idx, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
 // grid of double-float planes (FP64 plans with the double-float FFT): the plane-owner scheme
 // of k_grid_owner with the staged 2-D weights, the plane-weighted data and the accumulators as
 // double-float pairs, updated in pair arithmetic on the FP32 pipes (dd_fma), and the planes
@@ -589,11 +623,13 @@ __device__ __forceinline__ void owner_add_dd(const GridStageDD<G>* __restrict__ 
   }
 }
 
+// vis: the per-position data of k_grid_vis_dd (float4 pairs, 16 bytes like a double2), which
+// already carry the weights, the fold and the w-reference phase
 template <int G>
 __global__ void __launch_bounds__(kOwnerThreads)
 k_grid_owner_dd(const Geom g, const __grid_constant__ Coef<double> coef, const IndexView<double> ix,
-                const double2* __restrict__ vis, const double* __restrict__ wgt,
-                double2* __restrict__ planes, int b0, int nb, int bs, int pitch) {
+                const double2* __restrict__ vis, double2* __restrict__ planes, int b0, int nb,
+                int bs, int pitch) {
   extern __shared__ __align__(16) unsigned char smem[];
   double* sc = reinterpret_cast<double*>(smem);
   using Stage = GridStageDD<G>;
@@ -644,25 +680,10 @@ k_grid_owner_dd(const Geom g, const __grid_constant__ Coef<double> coef, const I
         stg->wv[v][j1] = make_float2(pv.h, pv.l);
         const dd wwj = g.do_w ? (lj ? kernel_value_dd(ix, sc, g.deg, vi, 2, j1, zz.w) : zero)
                               : (j1 == 0 ? dd_make(1.f, 0.f) : zero);
-        dd dr = zero, di = zero;
-        if (j1 == 0) {
-          const uint32_t id = ix.idx[vi];
-          const int64_t k = id & ~kFoldBit;
-          const double2 d = vis[k];
-          double xr = d.x, xi = d.y;
-          if (wgt != nullptr) { const double w = wgt[k]; xr *= w; xi *= w; }
-          if (id & kFoldBit) xi = -xi;      // grid conj(d) at the folded coordinates
-          if (ix.ph != nullptr) {           // times conj(exp(2 pi i w nshift))
-            const double2 ph = ix.ph[vi];
-            const double r = xr * ph.x + xi * ph.y;
-            xi = xi * ph.x - xr * ph.y;
-            xr = r;
-          }
-          dr = split_double(xr);
-          di = split_double(xi);
-        }
-        dr = dd_make(__shfl_sync(gmask, dr.h, 0, G), __shfl_sync(gmask, dr.l, 0, G));
-        di = dd_make(__shfl_sync(gmask, di.h, 0, G), __shfl_sync(gmask, di.l, 0, G));
+        // the visibility's weighted, folded and phase-rotated data, prepared once per call by
+        // k_grid_vis_dd as pairs in index order (`vis` holds them, 16 bytes per position)
+        const float4 q = reinterpret_cast<const float4*>(vis)[vi];
+        const dd dr = dd_make(q.x, q.y), di = dd_make(q.z, q.w);
         const dd qr = dd_mul(dr, wwj), qi = dd_mul(di, wwj);
         stg->dq[v][j1] = make_float4(qr.h, qr.l, qi.h, qi.l);
       }
@@ -970,7 +991,7 @@ static cudaError_t grid_owner_g(const Geom& g, const Coef<R>& coef, const IndexV
       cudaError_t e = cudaFuncSetAttribute(k_grid_owner_dd<G>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      k_grid_owner_dd<G><<<grid, kOwnerThreads, smem, s>>>(g, coef, ix, vis, wgt, planes, b0, nb, bs, pitch);
+      k_grid_owner_dd<G><<<grid, kOwnerThreads, smem, s>>>(g, coef, ix, vis, planes, b0, nb, bs, pitch);
       return cudaGetLastError();
     }
   }

@@ -220,7 +220,7 @@ static int make_fft1d(cufftHandle* h, int prec, int64_t n, int64_t stride, int64
 
 // per-call workspace layout
 struct Workspace {
-  size_t planes = 0, fft = 0, acc = 0, wts = 0, total = 0;   // acc: grid accumulator / degrid partials
+  size_t planes = 0, fft = 0, acc = 0, wts = 0, visd = 0, total = 0;   // acc: grid accumulator / degrid partials
 };
 
 static Workspace workspace_layout(const wg_plan* p, int64_t batch, size_t fft_ws) {
@@ -231,7 +231,9 @@ static Workspace workspace_layout(const wg_plan* p, int64_t batch, size_t fft_ws
   size_t partials = (size_t)p->nslot * std::max<int64_t>(1, p->nvis) * cplx_bytes(p->prec);
   w.acc = align_up(std::max(grid_acc, partials), 256);
   w.wts = p->use_wts ? align_up((size_t)std::max<int64_t>(1, p->nvis) * 3 * kMaxG * 8, 256) : 0;
-  w.total = w.planes + w.fft + w.acc + w.wts;
+  // double-float planes: the gridding's prepared visibility data, a pair per part and position
+  w.visd = p->g.df64_planes ? align_up((size_t)std::max<int64_t>(1, p->nvis) * 16, 256) : 0;
+  w.total = w.planes + w.fft + w.acc + w.wts + w.visd;
   return w;
 }
 
@@ -729,9 +731,20 @@ static int grid_impl(wg_plan* p, const typename C2<R>::T* vis, const R* wgt, R* 
       e = launch_weights<R>(g, coef, ix, p->nvis, wts_call, s);
       if (e != cudaSuccess) { rc = set_error(WG_ERR_CUDA, "weights: %s", cudaGetErrorString(e)); break; }
     }
+    // double-float planes: weights, fold and w-reference phase applied once, as pairs, and the
+    // gridding kernel reads those instead of vis / wgt
+    const typename C2<R>::T* vgrid = vis;
+    if constexpr (sizeof(R) == 8) {
+      if (g.df64_planes) {
+        auto* visd = (float4*)(ws + w.planes + w.fft + w.acc + w.wts);
+        e = launch_grid_vis_dd(ix, vis, wgt, p->nvis, visd, s);
+        if (e != cudaSuccess) { rc = set_error(WG_ERR_CUDA, "grid data: %s", cudaGetErrorString(e)); break; }
+        vgrid = (const typename C2<R>::T*)visd;
+      }
+    }
     for (int64_t b0 = 0; b0 < g.nw; b0 += p->batch) {
       int nb = (int)std::min<int64_t>(p->batch, g.nw - b0);
-      e = launch_grid<R>(g, coef, ix, vis, wgt, planes, (int)b0, nb, s);
+      e = launch_grid<R>(g, coef, ix, vgrid, wgt, planes, (int)b0, nb, s);
       if (e != cudaSuccess) { rc = set_error(WG_ERR_CUDA, "grid: %s", cudaGetErrorString(e)); break; }
       tm.mark(ST_GRID);
       if ((rc = run_fft(p, nb, planes, fftw, CUFFT_INVERSE, s)) != WG_OK) break;
@@ -751,7 +764,8 @@ static int grid_impl(wg_plan* p, const typename C2<R>::T* vis, const R* wgt, R* 
     tm.finish(stats);
     stats->n_batches = nbatches; stats->n_planes = g.nw; stats->workspace_bytes = w.total;
     // grid + accumulate per batch, weights; the double-float FFT's two passes per batch
-    stats->n_kernels = 2 * nbatches + (wts_call != nullptr) + (p->dfft != nullptr ? 2 * nbatches : 0);
+    stats->n_kernels = 2 * nbatches + (wts_call != nullptr) + (p->dfft != nullptr ? 2 * nbatches : 0) +
+                       (g.df64_planes ? 1 : 0);
     stats->n_fft_calls = nbatches;
   }
   return WG_OK;

@@ -121,9 +121,14 @@ template <typename R>
 cudaError_t launch_degrid_finalize(const Geom& g, const IndexView<R>& ix,
                                    const typename C2<R>::T* partial, int64_t nvis_idx, int bs,
                                    const R* wgt, typename C2<R>::T* vis, cudaStream_t s);
+// For double-float planes (g.df64_planes) `vis` is the output of launch_grid_vis_dd and `wgt`
+// is not used.
 template <typename R>
 cudaError_t launch_grid(const Geom& g, const Coef<R>& coef, const IndexView<R>& ix,
                         const typename C2<R>::T* vis, const R* wgt,
                         typename C2<R>::T* planes, int b0, int nb, cudaStream_t s);
+// weighted, folded, phase-rotated visibility data per index position as double-float pairs
+cudaError_t launch_grid_vis_dd(const IndexView<double>& ix, const double2* vis, const double* wgt,
+                               int64_t nvis_idx, float4* out, cudaStream_t s);
 
 }  // namespace wg
