@@ -118,9 +118,11 @@ def test_weights_and_mask(wg, oracle_lib):
     rng = np.random.default_rng(7)
     wgt = rng.uniform(0.2, 2.0, (333, 4))
     mask = (rng.uniform(size=(333, 4)) > 0.3).astype(np.uint8)
-    for prec, eps in (("f64", 1e-10), ("f32", 1e-5)):
-        _, vis, img = run_pair(wg, obs, eps, prec, I, d, wgt=wgt, mask=mask)
-        rv, ri = oracle_pair(oracle_lib, obs, I, d, wgt=wgt, mask=mask)
+    rv, ri = oracle_pair(oracle_lib, obs, I, d, wgt=wgt, mask=mask)
+    # FP64 with double-float planes (pair-arithmetic (de)gridding) and with cuFFT Z2Z planes
+    for prec, eps, fft in (("f64", 1e-10, 2), ("f64", 1e-10, 3), ("f32", 1e-5, 0)):
+        plan, vis, img = run_pair(wg, obs, eps, prec, I, d, wgt=wgt, mask=mask, fft_impl=fft)
+        assert fft == 0 or plan.info["fft_impl"] == fft
         assert oracle_lib.rel_l2(vis, rv) <= eps and oracle_lib.rel_l2(img, ri) <= eps
         assert np.all(vis[mask == 0] == 0)
 
@@ -129,10 +131,11 @@ def test_no_wstacking(wg, oracle_lib):
     obs = S.random_uvw_observation(400, 2, 64, 96, 20.0, seed=11)
     I = S.gaussian_image(64, 96, seed=6)
     d = S.complex_normal((400, 2), seed=7)
-    for prec, eps in (("f64", 1e-9), ("f32", 1e-5)):
-        plan, vis, img = run_pair(wg, obs, eps, prec, I, d, do_wstacking=False)
+    rv, ri = oracle_pair(oracle_lib, obs, I, d, do_wstacking=False)
+    for prec, eps, fft in (("f64", 1e-9, 2), ("f64", 1e-9, 3), ("f32", 1e-5, 0)):
+        plan, vis, img = run_pair(wg, obs, eps, prec, I, d, do_wstacking=False, fft_impl=fft)
         assert plan.info["nw"] == 1
-        rv, ri = oracle_pair(oracle_lib, obs, I, d, do_wstacking=False)
+        assert fft == 0 or plan.info["fft_impl"] == fft
         assert oracle_lib.rel_l2(vis, rv) <= eps and oracle_lib.rel_l2(img, ri) <= eps
 
 
