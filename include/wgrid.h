@@ -82,12 +82,16 @@ typedef struct wg_options {
   int tile;                /* uv tile side in cells (16 or 32; 0 = automatic) */
   int grid_variant;        /* gridding accumulation: 0 = automatic (shared-memory atomics for
                               WG_F32, plane-owner warps for WG_F64), 1 = shared-memory atomics,
-                              2 = plane-owner warps (deterministic) */
+                              2 = plane-owner warps (deterministic); WG_F64 plans with the
+                              double-float FFT always use plane-owner warps (their planes are
+                              double-float pairs, written by that kernel only) */
   int fft_impl;            /* plane FFTs: 0 = automatic (WG_F32: cuFFT C2C; WG_F64: the
                               cheaper of 2 and 3 whose predicted error fits epsilon),
                               1 = cuFFT 2-D, 2 = the library's double-float FFT (WG_F64 only,
                               grid sides <= 6400; its ~5e-15 rounding is amplified by the
-                              1 / psi correction, so the planner may raise sigma for it),
+                              1 / psi correction, so the planner may raise sigma for it; the
+                              uv planes are then kept as double-float pairs and (de)gridded in
+                              pair arithmetic),
                               3 = pruned cuFFT Z2Z (WG_F64 only: 1-D passes that skip the
                               plane rows outside the image) */
 } wg_options;
