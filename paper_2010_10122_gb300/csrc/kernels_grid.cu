@@ -389,16 +389,20 @@ __device__ __forceinline__ void owner_add(const GridStage<R, G>* __restrict__ st
     wt[m] = ok ? stg->wt[v][c] : (R)0;
     off[m] = ok ? (fp.ru + i) * pitch + fp.rv + j : dummy;
   }
+  // loads, arithmetic and stores in separate sweeps (see owner_add_dd)
   for (int pl = p1; pl < phi; pl += kOwnerWarps) {
     const CT dq = stg->dq[v][pl + qoff];
     CT* base = acc + pl * plane_elems;
+    CT a[MC];
+#pragma unroll
+    for (int m = 0; m < MC; ++m) a[m] = base[off[m]];
 #pragma unroll
     for (int m = 0; m < MC; ++m) {
-      CT a = base[off[m]];
-      a.x = fma(dq.x, wt[m], a.x);
-      a.y = fma(dq.y, wt[m], a.y);
-      base[off[m]] = a;
+      a[m].x = fma(dq.x, wt[m], a[m].x);
+      a[m].y = fma(dq.y, wt[m], a[m].y);
     }
+#pragma unroll
+    for (int m = 0; m < MC; ++m) base[off[m]] = a[m];
   }
 }
 
@@ -610,16 +614,23 @@ __device__ __forceinline__ void owner_add_dd(const GridStageDD<G>* __restrict__ 
     wt[m] = ok ? dd_mul(dd_make(a.x, a.y), dd_make(b.x, b.y)) : dd_make(0.f, 0.f);
     off[m] = ok ? (fp.ru + i) * pitch + fp.rv + j : dummy;
   }
+  // all loads of a plane first, then the arithmetic, then all stores: the cells of one lane are
+  // distinct (its idle slots share a padding cell, updated with weight 0), but the compiler
+  // cannot see that, and interleaved load / store would serialise the MC update chains
   for (int pl = p1; pl < phi; pl += kOwnerWarps) {
     const float4 q = stg->dq[v][pl + qoff];
     float4* base = acc + pl * plane_elems;
+    float4 a[MC];
+#pragma unroll
+    for (int m = 0; m < MC; ++m) a[m] = base[off[m]];
 #pragma unroll
     for (int m = 0; m < MC; ++m) {
-      float4 a = base[off[m]];
-      const dd re = dd_fma(dd_make(q.x, q.y), wt[m], dd_make(a.x, a.y));
-      const dd im = dd_fma(dd_make(q.z, q.w), wt[m], dd_make(a.z, a.w));
-      base[off[m]] = make_float4(re.h, re.l, im.h, im.l);
+      const dd re = dd_fma(dd_make(q.x, q.y), wt[m], dd_make(a[m].x, a[m].y));
+      const dd im = dd_fma(dd_make(q.z, q.w), wt[m], dd_make(a[m].z, a[m].w));
+      a[m] = make_float4(re.h, re.l, im.h, im.l);
     }
+#pragma unroll
+    for (int m = 0; m < MC; ++m) base[off[m]] = a[m];
   }
 }
 
