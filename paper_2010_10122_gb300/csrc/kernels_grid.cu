@@ -244,19 +244,45 @@ k_degrid_dd(const Geom g, const __grid_constant__ Coef<double> coef, const Index
   const int j = threadIdx.x & (G - 1);
   const int grp = threadIdx.x / G, ngrp = blockDim.x / G;
   const dd zero = dd_make(0.f, 0.f);
-  for (uint32_t v0 = lo + (threadIdx.x >> 5) * (32 / G); v0 < hi; v0 += ngrp) {
-    const uint32_t vi = v0 + (grp % (32 / G));
+  // with a kernel-value table, the group's next visibility's index entry and table values are
+  // loaded while the current one is summed (the loads' latency is otherwise exposed)
+  const float2* tw = reinterpret_cast<const float2*>(ix.wts);
+  const uint32_t gofs = grp % (32 / G);
+  uint32_t mt_n = 0;
+  float2 pu_n = make_float2(0.f, 0.f), pv_n = pu_n, pw_n = pu_n;
+  auto prefetch = [&](uint32_t vi) {
+    if (vi < hi) {
+      mt_n = ix.meta[vi];
+      if (tw != nullptr && j < alpha) {
+        const int64_t b = (int64_t)vi * (3 * kMaxG) + j;
+        pu_n = tw[b]; pv_n = tw[b + kMaxG]; pw_n = tw[b + 2 * kMaxG];
+      }
+    }
+  };
+  uint32_t v0 = lo + (threadIdx.x >> 5) * (32 / G);
+  prefetch(v0 + gofs);
+  for (; v0 < hi; v0 += ngrp) {
+    const uint32_t vi = v0 + gofs;
     const bool act = vi < hi;
-    uint32_t mt = 0;
+    const uint32_t mt = act ? mt_n : 0u;
+    const float2 tu = pu_n, tv = pv_n, tww = pw_n;
+    prefetch(v0 + ngrp + gofs);
     Z4<double> zz;
     zz.u = zz.v = zz.w = zz.pad = 0.0;
-    if (act) { mt = ix.meta[vi]; if (ix.wts == nullptr) zz = ix.z[vi]; }
+    if (act && tw == nullptr) zz = ix.z[vi];
     const int du = mt & 255, dv = (mt >> 8) & 255, c0 = (int)(mt >> 16);
     const bool lj = act && j < alpha;
-    const dd pu = lj ? kernel_value_dd(ix, sc, g.deg, vi, 0, j, zz.u) : zero;
-    const dd pv = lj ? kernel_value_dd(ix, sc, g.deg, vi, 1, j, zz.v) : zero;
-    const dd pw = g.do_w ? (lj ? kernel_value_dd(ix, sc, g.deg, vi, 2, j, zz.w) : zero)
-                         : (j == 0 ? dd_make(1.f, 0.f) : zero);
+    dd pu = zero, pv = zero, pw = zero;
+    if (lj) {
+      if (tw != nullptr) {
+        pu = dd_make(tu.x, tu.y); pv = dd_make(tv.x, tv.y); pw = dd_make(tww.x, tww.y);
+      } else {
+        pu = kernel_value_dd(ix, sc, g.deg, vi, 0, j, zz.u);
+        pv = kernel_value_dd(ix, sc, g.deg, vi, 1, j, zz.v);
+        pw = kernel_value_dd(ix, sc, g.deg, vi, 2, j, zz.w);
+      }
+    }
+    if (!g.do_w) pw = j == 0 ? dd_make(1.f, 0.f) : zero;
     dd wu[G];
 #pragma unroll
     for (int i = 0; i < G; ++i) wu[i] = shfl_dd(pu, i, G);
