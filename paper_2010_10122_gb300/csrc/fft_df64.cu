@@ -16,6 +16,7 @@
 // the first pass splits doubles into df64 on load and stores df64, the second loads df64 and
 // joins back to doubles on store.  Transforms are unnormalised, forward = e^{-2 pi i}, like
 // cuFFT's.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -136,7 +137,6 @@ __device__ __forceinline__ void butterfly(cdd* x, bool fwd, const FftLine& L) {
   else dft_generic<R>(x, fwd, L.tw, L.n);
 }
 
-constexpr int kLoadBatch = 4;   // line elements a thread loads at once
 
 // One radix-R Stockham stage of a length-n line: butterfly j (j = tid, tid + T, ...) reads
 // src[j + kk M], twiddles, transforms and writes dst[(j / Ns) Ns R + j mod Ns + q Ns].
@@ -167,93 +167,151 @@ __device__ __forceinline__ void stage(const float4* __restrict__ src, float4* __
   }
 }
 
-// Transform one line per CTA: line `line` of plane `plane`, element i at global offset
+constexpr int kLoadBatch = 4;   // doubles a thread loads at once (mode 0)
+
+// 16-byte asynchronous global -> shared copies (cp.async): a line's load is issued before the
+// previous line's store, so the two overlap
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Transform lines g = blockIdx.x, blockIdx.x + gridDim.x, ... < nlines (a persistent CTA): line
+// g is line g mod lines_per_plane of plane g / lines_per_plane, element i at global offset
 // plane * plane_elems + line * line_stride + i * elem_stride (complex elements).  The plane's
-// transformed lines are numbered 0 .. lines_per_plane - 1; those from `split` on are shifted
-// by `skip` (a pass over the first and last rows of a plane only, skipping the middle).
-// mode 0: load doubles, store df64; mode 1: load df64, store doubles; mode 2: load and store df64.  Elements lhalf ..
-// n - lhalf - 1 are known zeros and not loaded, elements shalf .. n - shalf - 1 are not stored
-// (lhalf = shalf = n: everything).  Two n-element
-// shared-memory buffers (ping-pong); kAll adds the rare radices 2, 7 and 11, kept out of the
-// common instance so that its register allocation is not burdened with them.
-template <int TMAX, int MINB, bool kAll>
+// lines from `split` on are shifted by `skip` (a pass over the first and last rows of a plane
+// only, skipping the middle).  mode 0: load doubles, store df64; mode 1: load df64, store
+// doubles; mode 2: load and store df64.  Elements lhalf .. n - lhalf - 1 are known zeros and not
+// loaded, elements shalf .. n - shalf - 1 are not stored (lhalf = shalf = n: everything).  Two
+// n-element shared-memory buffers (ping-pong); with kAsync, after the last stage the buffer the
+// stages no longer read receives the next line (asynchronous copies) while the result is stored
+// (a line loaded through registers, kAsync false, gains nothing from it: those launches run one
+// line per CTA).  kAll
+// adds the rare radices 2, 7 and 11, kept out of the common instance so that its register
+// allocation is not burdened with them.
+template <int TMAX, int MINB, bool kAll, bool kAsync>
 __global__ void __launch_bounds__(TMAX, MINB)
 k_fft_lines(const __grid_constant__ FftLine L, void* __restrict__ data, int64_t plane_elems,
             int lines_per_plane, int64_t line_stride, int64_t elem_stride, int mode, int fwd,
-            int split, int skip, int lhalf, int shalf) {
+            int split, int skip, int lhalf, int shalf, int64_t nlines) {
   extern __shared__ __align__(16) float4 fsm[];
   const int n = L.n;
   const int T = blockDim.x;
   const int swz = (n & 7) == 0 ? 7 : 0;
   float4* src = fsm;
   float4* dst = fsm + n;
-  const int plane = blockIdx.x / lines_per_plane;
-  int line = blockIdx.x - plane * lines_per_plane;
-  if (line >= split) line += skip;
-  const int64_t base = (int64_t)plane * plane_elems + (int64_t)line * line_stride;
-  // load the line: kLoadBatch elements per thread in flight at once (a column is a strided
-  // gather)
-  for (int i0 = threadIdx.x; i0 < n; i0 += kLoadBatch * T) {
-    float4 v[kLoadBatch];
-#pragma unroll
-    for (int k = 0; k < kLoadBatch; ++k) {
-      const int i = i0 + k * T;
-      if (i < n) {
-        if (i < lhalf || i >= n - lhalf)
-          v[k] = reinterpret_cast<const float4*>(data)[base + i * elem_stride];
-        else
-          v[k] = make_float4(0.f, 0.f, 0.f, 0.f);   // known zero: not loaded
+  auto line_base = [&](int64_t gl) -> int64_t {
+    const int64_t plane = gl / lines_per_plane;
+    int line = (int)(gl - plane * lines_per_plane);
+    if (line >= split) line += skip;
+    return plane * plane_elems + (int64_t)line * line_stride;
+  };
+  // line gl into buffer b, each thread its elements i = tid, tid + T, ...; known zeros are
+  // written directly.  kAsync (pairs, modes 1 and 2): asynchronous copies, completed by the
+  // thread's cp_async_wait_all.  Otherwise loaded kLoadBatch at a time through registers, doubles
+  // (mode 0) split into float pairs on the way.
+  auto issue = [&](int64_t gl, float4* b) {
+    const int64_t base = line_base(gl);
+    const float4* g4 = reinterpret_cast<const float4*>(data);
+    if (kAsync) {
+      for (int i = threadIdx.x; i < n; i += T) {
+        float4* d = b + swizzle(i, swz);
+        if (i < lhalf || i >= n - lhalf) cp_async16(d, g4 + base + i * elem_stride);
+        else *d = make_float4(0.f, 0.f, 0.f, 0.f);
       }
+      cp_async_commit();
+      return;
     }
+    for (int i0 = threadIdx.x; i0 < n; i0 += kLoadBatch * T) {
+      float4 v[kLoadBatch];
 #pragma unroll
-    for (int k = 0; k < kLoadBatch; ++k) {
-      const int i = i0 + k * T;
-      if (i < n) {
-        if (mode == 0) {
-          double2 d = make_double2(__hiloint2double(__float_as_int(v[k].y), __float_as_int(v[k].x)),
-                                   __hiloint2double(__float_as_int(v[k].w), __float_as_int(v[k].z)));
-          cdd x; x.r = split_double(d.x); x.i = split_double(d.y);
-          src[swizzle(i, swz)] = store_cdd(x);
-        } else {
-          src[swizzle(i, swz)] = v[k];
+      for (int k = 0; k < kLoadBatch; ++k) {
+        const int i = i0 + k * T;
+        if (i < n) v[k] = (i < lhalf || i >= n - lhalf) ? g4[base + i * elem_stride]
+                                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int k = 0; k < kLoadBatch; ++k) {
+        const int i = i0 + k * T;
+        if (i < n) {
+          if (mode == 0) {
+            const double2 d = make_double2(__hiloint2double(__float_as_int(v[k].y), __float_as_int(v[k].x)),
+                                           __hiloint2double(__float_as_int(v[k].w), __float_as_int(v[k].z)));
+            cdd x; x.r = split_double(d.x); x.i = split_double(d.y);
+            b[swizzle(i, swz)] = store_cdd(x);
+          } else {
+            b[swizzle(i, swz)] = v[k];
+          }
         }
       }
     }
-  }
-  __syncthreads();
-  int Ns = 1;
+  };
   const bool f = fwd != 0;
-  for (int s = 0; s < L.nst; ++s) {
-    const int R = L.radix[s];
-    switch (R) {
-      case 3: stage<3>(src, dst, n, Ns, f, L, swz); break;
-      case 4: stage<4>(src, dst, n, Ns, f, L, swz); break;
-      case 5: stage<5>(src, dst, n, Ns, f, L, swz); break;
-      case 8: stage<8>(src, dst, n, Ns, f, L, swz); break;
-      default:
-        if (kAll) {
-          if (R == 2) stage<2>(src, dst, n, Ns, f, L, swz);
-          else if (R == 7) stage<7>(src, dst, n, Ns, f, L, swz);
-          else stage<11>(src, dst, n, Ns, f, L, swz);
-        }
-        break;
+  // the radix stages in the two buffers; the result ends in src
+  auto run_stages = [&]() {
+    int Ns = 1;
+    for (int s = 0; s < L.nst; ++s) {
+      const int R = L.radix[s];
+      switch (R) {
+        case 3: stage<3>(src, dst, n, Ns, f, L, swz); break;
+        case 4: stage<4>(src, dst, n, Ns, f, L, swz); break;
+        case 5: stage<5>(src, dst, n, Ns, f, L, swz); break;
+        case 8: stage<8>(src, dst, n, Ns, f, L, swz); break;
+        default:
+          if (kAll) {
+            if (R == 2) stage<2>(src, dst, n, Ns, f, L, swz);
+            else if (R == 7) stage<7>(src, dst, n, Ns, f, L, swz);
+            else stage<11>(src, dst, n, Ns, f, L, swz);
+          }
+          break;
+      }
+      __syncthreads();
+      float4* t = src; src = dst; dst = t;
+      Ns *= R;
     }
+  };
+  auto store_line = [&](int64_t base) {
+    if (mode != 1) {
+      float4* out = reinterpret_cast<float4*>(data) + base;
+      for (int i = threadIdx.x; i < n; i += T)
+        if (i < shalf || i >= n - shalf) out[i * elem_stride] = src[swizzle(i, swz)];
+    } else {
+      double2* out = reinterpret_cast<double2*>(data) + base;
+      for (int i = threadIdx.x; i < n; i += T) {
+        if (i >= shalf && i < n - shalf) continue;   // not needed downstream
+        cdd x = load_cdd(src[swizzle(i, swz)]);
+        double2 v; v.x = join_double(x.r); v.y = join_double(x.i);
+        out[i * elem_stride] = v;
+      }
+    }
+  };
+  int64_t gl = blockIdx.x;
+  if (gl >= nlines) return;
+  if constexpr (!kAsync) {   // one line per CTA
+    issue(gl, src);
     __syncthreads();
-    float4* t = src; src = dst; dst = t;
-    Ns *= R;
+    run_stages();
+    store_line(line_base(gl));
+    return;
   }
-  if (mode != 1) {
-    float4* out = reinterpret_cast<float4*>(data) + base;
-    for (int i = threadIdx.x; i < n; i += T)
-      if (i < shalf || i >= n - shalf) out[i * elem_stride] = src[swizzle(i, swz)];
-  } else {
-    double2* out = reinterpret_cast<double2*>(data) + base;
-    for (int i = threadIdx.x; i < n; i += T) {
-      if (i >= shalf && i < n - shalf) continue;   // not needed downstream
-      cdd x = load_cdd(src[swizzle(i, swz)]);
-      double2 v; v.x = join_double(x.r); v.y = join_double(x.i);
-      out[i * elem_stride] = v;
-    }
+  issue(gl, src);
+  cp_async_wait_all();
+  __syncthreads();
+  for (;;) {
+    run_stages();
+    // the result is in src; dst is no longer read: the next line's copies go there while the
+    // result is stored
+    const int64_t gn = gl + gridDim.x;
+    const bool more = gn < nlines;
+    if (more) issue(gn, dst);
+    store_line(line_base(gl));
+    if (!more) break;
+    cp_async_wait_all();
+    __syncthreads();   // the next line is in place everywhere, and src is no longer read
+    float4* t = src; src = dst; dst = t;
+    gl = gn;
   }
 }
 
@@ -317,10 +375,14 @@ cudaError_t df64_fft_create(int64_t nu, int64_t nv, Df64Fft** out) {
   cudaError_t e = make_line((int)nu, &f->lu, &f->tw_u);
   if (e == cudaSuccess) e = make_line((int)nv, &f->lv, &f->tw_v);
   const int smax = (int)(2 * kMaxSide * sizeof(float4));
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft_lines<448, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft_lines<448, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft_lines<832, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fft_lines<832, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+#define WG_SMEM_ATTR(TM, MB, A, Y)                                                              \
+  if (e == cudaSuccess)                                                                         \
+    e = cudaFuncSetAttribute(k_fft_lines<TM, MB, A, Y>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax)
+  WG_SMEM_ATTR(448, 2, false, false); WG_SMEM_ATTR(448, 2, false, true);
+  WG_SMEM_ATTR(448, 2, true, false);  WG_SMEM_ATTR(448, 2, true, true);
+  WG_SMEM_ATTR(832, 1, false, false); WG_SMEM_ATTR(832, 1, false, true);
+  WG_SMEM_ATTR(832, 1, true, false);  WG_SMEM_ATTR(832, 1, true, true);
+#undef WG_SMEM_ATTR
   if (e != cudaSuccess) {
     if (f->tw_u) cudaFree(f->tw_u);
     if (f->tw_v) cudaFree(f->tw_v);
@@ -344,20 +406,34 @@ static cudaError_t launch_lines(const FftLine& L, double2* data, int64_t batch, 
                                 cudaStream_t s) {
   if (lines_per_plane == 0 || batch == 0) return cudaSuccess;
   const size_t smem = 2 * sizeof(float4) * (size_t)L.n;
-  const int64_t blocks = batch * lines_per_plane;
+  const int64_t nlines = batch * lines_per_plane;
+  // persistent CTAs: as many as fit the GPU at once (two per SM up to 448 threads, else one)
+  int dev = 0, sms = 0;
+  cudaError_t ea = cudaGetDevice(&dev);
+  if (ea == cudaSuccess) ea = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (ea != cudaSuccess) return ea;
+  // pairs in, every element loaded: persistent CTAs with asynchronous loads (inverse row pass
+  // 40.8 -> 38.5 ms per bench grid call); doubles in (converted on load) or pruned loads: one
+  // line per CTA (the persistent form measured 1.2 ms slower on the forward row pass)
+  const bool async = mode != 0 && 2 * (int64_t)lhalf >= L.n;
+  const int64_t blocks =
+      async ? std::min<int64_t>(nlines, (int64_t)sms * (L.threads <= 448 ? 2 : 1)) : nlines;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
   bool common = true;   // radices 8, 4, 5, 3 only
   for (int i = 0; i < L.nst; ++i)
     if (L.radix[i] == 2 || L.radix[i] == 7 || L.radix[i] == 11) common = false;
-#define WG_LINES(TM, MB, A)                                                                     \
-  k_fft_lines<TM, MB, A><<<(unsigned)blocks, L.threads, smem, s>>>(                             \
+#define WG_LINES1(TM, MB, A, Y)                                                                 \
+  k_fft_lines<TM, MB, A, Y><<<(unsigned)blocks, L.threads, smem, s>>>(                          \
       L, data, plane, lines_per_plane, line_stride, elem_stride, mode, fwd, split, skip, lhalf, \
-      shalf)
+      shalf, nlines)
+#define WG_LINES(TM, MB, A) \
+  if (async) WG_LINES1(TM, MB, A, true); else WG_LINES1(TM, MB, A, false)
   if (L.threads <= 448) {
-    if (common) WG_LINES(448, 2, false); else WG_LINES(448, 2, true);
+    if (common) { WG_LINES(448, 2, false); } else { WG_LINES(448, 2, true); }
   } else {
-    if (common) WG_LINES(832, 1, false); else WG_LINES(832, 1, true);
+    if (common) { WG_LINES(832, 1, false); } else { WG_LINES(832, 1, true); }
   }
+#undef WG_LINES1
 #undef WG_LINES
   return cudaGetLastError();
 }
