@@ -255,9 +255,9 @@ def df64_line_ops(n):
 
 
 # DRAM bytes the double-float FFT moved per algorithmic byte (one 16-byte read and one 16-byte
-# write per cell and pass), measured by ncu on full 3456^2 transforms: 30.8 of 32 B per cell
+# write per cell and pass), measured by ncu on full 3456^2 transforms: 31.1 of 32 B per cell
 # and pass (profiles/k_fft_lines_df64_3456.md); the rest stays in L2 when the kernel ends
-DF64_DRAM_PER_ALGORITHMIC_BYTE = 30.8 / 32.0
+DF64_DRAM_PER_ALGORITHMIC_BYTE = 31.1 / 32.0
 
 
 def df64_fft_bytes(nx, ny, nu, nv, direction):
