@@ -23,6 +23,22 @@ namespace wg {
 
 constexpr int kThreads = 256;
 
+
+// asynchronous 8- or 16-byte global -> shared copy (cp.async) of one plane cell; completed by
+// stage_wait() before the block's barrier
+template <typename CT>
+__device__ __forceinline__ void stage_copy(CT* d, const CT* g) {
+  static_assert(sizeof(CT) == 8 || sizeof(CT) == 16, "plane cell size");
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(d);
+  if (sizeof(CT) == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(g) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(g) : "memory");
+}
+__device__ __forceinline__ void stage_wait() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 template <typename R>
 __device__ __forceinline__ R horner(const R* __restrict__ sc, int deg, int j, R z) {
   R r = sc[deg * kMaxG + j];
@@ -119,9 +135,10 @@ k_degrid(const Geom g, const __grid_constant__ Coef<R> coef, const IndexView<R> 
       int r = e / TH, c = e - r * TH;
       int gu = tu * T + r; if (gu >= g.nu) gu -= g.nu;
       int gv = tv * T + c; if (gv >= g.nv) gv -= g.nv;
-      dst[e] = src[(int64_t)gu * g.nv + gv];
+      stage_copy(dst + e, src + (int64_t)gu * g.nv + gv);
     }
   }
+  stage_wait();
   __syncthreads();
   // G lanes per visibility (lane j = piece / footprint column j).  Visibilities of a tile are
   // sorted by first plane, so the groups of a warp have nearly the same plane range: the plane
@@ -237,9 +254,10 @@ k_degrid_dd(const Geom g, const __grid_constant__ Coef<double> coef, const Index
       int r = e / TH, c = e - r * TH;
       int gu = tu * T + r; if (gu >= g.nu) gu -= g.nu;
       int gv = tv * T + c; if (gv >= g.nv) gv -= g.nv;
-      dst[e] = src[(int64_t)gu * g.nv + gv];       // 16 bytes, copied as they are
+      stage_copy(dst + e, src + (int64_t)gu * g.nv + gv);   // 16 bytes, copied as they are
     }
   }
+  stage_wait();
   __syncthreads();
   const int j = threadIdx.x & (G - 1);
   const int grp = threadIdx.x / G, ngrp = blockDim.x / G;
