@@ -718,6 +718,17 @@ k_grid_owner_dd(const Geom g, const __grid_constant__ Coef<double> coef, const I
       for (int v = grp; v < nch; v += ngrp) {
         const uint32_t vi = cs + v;
         const uint32_t mt = ix.meta[vi];
+        // with a kernel-value table, the visibility's table entries and data are loaded
+        // together with its index entry (before the tile test), so their latencies overlap
+        const float2* tw = reinterpret_cast<const float2*>(ix.wts);
+        float2 tu = make_float2(0.f, 0.f), tv = tu, tww = tu;
+        if (tw != nullptr) {
+          const int64_t b = (int64_t)vi * (3 * kMaxG) + j1;
+          tu = tw[b]; tv = tw[b + kMaxG]; tww = tw[b + 2 * kMaxG];
+        }
+        // the visibility's weighted, folded and phase-rotated data, prepared once per call by
+        // k_grid_vis_dd as pairs in index order (`vis` holds them, 16 bytes per position)
+        const float4 q = reinterpret_cast<const float4*>(vis)[vi];
         const int ru = (int)(mt & 255) + ou * T, rv = (int)((mt >> 8) & 255) + ov * T;
         const bool hit = (ru + alpha > 0) && (rv + alpha > 0);
         if (j1 == 0) {
@@ -725,19 +736,21 @@ k_grid_owner_dd(const Geom g, const __grid_constant__ Coef<double> coef, const I
           stg->c0[v] = hit ? (int)(mt >> 16) : -(1 << 20);
         }
         if (!hit) continue;   // uniform within the group
-        Z4<double> zz;
-        zz.u = zz.v = zz.w = zz.pad = 0.0;
-        if (ix.wts == nullptr) zz = ix.z[vi];
         const bool lj = j1 < alpha;
-        const dd pu = lj ? kernel_value_dd(ix, sc, g.deg, vi, 0, j1, zz.u) : zero;
-        const dd pv = lj ? kernel_value_dd(ix, sc, g.deg, vi, 1, j1, zz.v) : zero;
+        dd pu = zero, pv = zero, pw = zero;
+        if (lj) {
+          if (tw != nullptr) {   // the table holds zeros beyond alpha as well
+            pu = dd_make(tu.x, tu.y); pv = dd_make(tv.x, tv.y); pw = dd_make(tww.x, tww.y);
+          } else {
+            const Z4<double> zz = ix.z[vi];
+            pu = kernel_value_dd(ix, sc, g.deg, vi, 0, j1, zz.u);
+            pv = kernel_value_dd(ix, sc, g.deg, vi, 1, j1, zz.v);
+            pw = kernel_value_dd(ix, sc, g.deg, vi, 2, j1, zz.w);
+          }
+        }
         stg->wu[v][j1] = make_float2(pu.h, pu.l);
         stg->wv[v][j1] = make_float2(pv.h, pv.l);
-        const dd wwj = g.do_w ? (lj ? kernel_value_dd(ix, sc, g.deg, vi, 2, j1, zz.w) : zero)
-                              : (j1 == 0 ? dd_make(1.f, 0.f) : zero);
-        // the visibility's weighted, folded and phase-rotated data, prepared once per call by
-        // k_grid_vis_dd as pairs in index order (`vis` holds them, 16 bytes per position)
-        const float4 q = reinterpret_cast<const float4*>(vis)[vi];
+        const dd wwj = g.do_w ? pw : (j1 == 0 ? dd_make(1.f, 0.f) : zero);
         const dd dr = dd_make(q.x, q.y), di = dd_make(q.z, q.w);
         const dd qr = dd_mul(dr, wwj), qi = dd_mul(di, wwj);
         stg->dq[v][j1] = make_float4(qr.h, qr.l, qi.h, qi.l);
