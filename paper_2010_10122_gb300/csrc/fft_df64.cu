@@ -1,6 +1,6 @@
 // 2-D complex FFT of FP64 planes computed in double-float ("df64") arithmetic on the FP32 pipes.
 //
-// GB300 executes FP64 FMAs at ~1/58 of its FP32 rate, which makes cuFFT's double-precision
+// GB300 executes FP64 FMAs at 1/64 of its FP32 rate, which makes cuFFT's double-precision
 // transforms the dominant cost of the FP64 (eps ~ 1e-12) mode.  Here every value is carried as
 // an unevaluated sum hi + lo of two floats (48-bit significand); additions use the two-sum and
 // products the fma-based two-product error-free transformations, so a radix-8 butterfly costs a
@@ -11,11 +11,13 @@
 // Algorithm: each 1-D transform is a mixed-radix (8 and 4 for the power of two, 5, 3, a
 // generic radix for 7 / 11, 2 only for n = 2 * odd) Stockham autosort FFT run by one CTA per
 // line with about n / 8 threads (one radix-8 butterfly each) over two n-element shared-memory
-// buffers (ping-pong); up to n = 3584 two CTAs share an SM.  The 2-D plane transform is a pass
-// over rows (contiguous) and a pass over columns.  Planes stay complex128 in global memory:
-// the first pass splits doubles into df64 on load and stores df64, the second loads df64 and
-// joins back to doubles on store.  Transforms are unnormalised, forward = e^{-2 pi i}, like
-// cuFFT's.
+// buffers (ping-pong); up to n = 3584 two CTAs share an SM.  A pass that reads float pairs in
+// full runs persistent CTAs instead, which copy their next line into the free buffer (cp.async)
+// while storing the current one.  The 2-D plane transform is a pass over rows (contiguous) and a
+// pass over columns.  On the image side planes are complex128 (the pass that reads them splits
+// doubles into float pairs on load, the pass that writes them joins the pairs back); on the uv
+// side they are complex128 or, for the (de)gridding kernels in pair arithmetic, float pairs.
+// Transforms are unnormalised, forward = e^{-2 pi i}, like cuFFT's.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
