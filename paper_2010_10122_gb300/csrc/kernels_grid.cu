@@ -15,7 +15,9 @@
 //    footprints reach into it, then writes every cell exactly once (no global atomics, no
 //    separate zeroing pass; empty tiles write zeros).  Two accumulation schemes: shared-memory
 //    atomics (cheap in FP32) or warps that each own whole planes (no atomics, deterministic;
-//    used for FP64, where shared-memory double atomics occupy the FP64 pipe).
+//    used for FP64, where shared-memory double atomics occupy the FP64 pipe);
+//  * FP64 plans with the double-float FFT keep the planes as double-float pairs and run the
+//    degridding and plane-owner gridding in pair arithmetic on the FP32 pipes (df64.cuh).
 #include "df64.cuh"
 #include "wgrid_internal.h"
 
