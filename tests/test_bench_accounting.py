@@ -1,0 +1,39 @@
+"""The benchmark's roofline accounting (host arithmetic, no GPU): the double-float FFT's radix
+plan and FP32 instruction count, its algorithmic bytes in the pruned form, and the (de)gridding
+flop count per visibility.  The roofline fractions the benchmark reports rest on these."""
+import bench
+
+
+def test_df64_radix_plan_matches_the_library_rule():
+    # powers of two as radix 8 and 4 (2 only for n = 2 * odd), then 5, 3, 7, 11
+    assert bench.df64_radices(3456) == [8, 4, 4, 3, 3, 3]
+    assert bench.df64_radices(2048) == [8, 8, 8, 4]
+    assert bench.df64_radices(2 * 27) == [2, 3, 3, 3]
+
+
+def test_df64_line_ops_per_element():
+    # 456 FP32 instructions per element of a 3456-point line (radix-8 butterfly 600, radix 4
+    # 176, radix 3 160, 38 per non-trivial twiddle product)
+    assert bench.df64_line_ops(3456) == 456 * 3456
+    # a single radix-8 stage has no twiddles: one butterfly per 8 elements
+    assert bench.df64_line_ops(8) == 600
+
+
+def test_df64_fft_bytes_pruned_and_full():
+    nx = ny = 2048
+    nu = nv = 3456
+    # full transform: one 16-byte read and one write per cell and pass
+    assert bench.df64_fft_bytes(nu, nv, nu, nv, "degrid") == 2 * 32 * nu * nv
+    assert bench.df64_fft_bytes(nu, nv, nu, nv, "grid") == 2 * 32 * nu * nv
+    # pruned: both directions move the same bytes (loads pruned forward, stores pruned inverse)
+    d = bench.df64_fft_bytes(nx, ny, nu, nv, "degrid")
+    assert d == bench.df64_fft_bytes(nx, ny, nu, nv, "grid")
+    assert d == 16 * (nx * ny + nu * ny) + 16 * (nu * ny + nu * nv)
+    assert d < 2 * 32 * nu * nv
+
+
+def test_gridding_flops_per_visibility():
+    # alpha^3 complex-by-real multiply-adds (4 flops) plus 3 alpha Horner evaluations of degree
+    # alpha + 3 (2 flops per step)
+    for a in (4, 8, 15, 16):
+        assert bench.algorithmic_flops_per_vis(a) == 4 * a ** 3 + 6 * a * (a + 3)
