@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--serve-load", type=float, default=0.9,
                     help="Poisson arrival rate as a fraction of the one-at-a-time capacity")
+    ap.add_argument("--modes-1e8", default="f32,f64",
+                    help="modes of the 1e8-visibility block (empty string: skip it)")
+    ap.add_argument("--steps-1e8", type=int, default=2)
     ap.add_argument("--only", default=None,
                     help="profiling aid: run only one call per step, e.g. f64:grid or f32:degrid")
     return ap.parse_args()
@@ -133,29 +136,33 @@ class ClockSampler:
 def oracle_rate(obs, I, d, seconds):
     """Direct-sum terms per second of the oracle on this host, measured on a bounded sample:
     degrid of a few visibilities (each a sum over all pixels) and grid of a few pixels (each
-    a sum over all visibilities).  Returns (vis_per_s, cores, sample description)."""
+    a sum over all visibilities), on all host cores and on one core.  Returns (vis_per_s,
+    cores, sample description, step seconds, vis_per_s on one core)."""
     from oracle import direct
     direct.build()
     rng = np.random.default_rng(0)
     npix = obs.npix_x * obs.npix_y
     nnz = int(np.count_nonzero(I))     # the oracle skips zero pixels in degrid
-    # calibrate: one visibility
+    # one core: a few visibilities and pixels on one thread (also the calibration)
+    v1 = rng.choice(obs.nvis, size=8, replace=False)
     t0 = time.perf_counter()
-    direct.degrid(obs.uvw, obs.freq, I, obs.pixsize_x, obs.pixsize_y, vis_index=np.array([0]), nthreads=1)
-    t1 = time.perf_counter() - t0
+    direct.degrid(obs.uvw, obs.freq, I, obs.pixsize_x, obs.pixsize_y, vis_index=v1, nthreads=1)
+    t1v = (time.perf_counter() - t0) / len(v1)
+    p1 = rng.choice(npix, size=2, replace=False)
+    t0 = time.perf_counter()
+    direct.grid(obs.uvw, obs.freq, d, obs.npix_x, obs.npix_y, obs.pixsize_x, obs.pixsize_y,
+                pixel_index=p1, nthreads=1)
+    t1p = (time.perf_counter() - t0) / len(p1)
+    step1 = 2 * (obs.nvis * t1v + npix * t1p)
     cores = direct.threads_used(0)
-    nv = int(max(cores, min(200000, 0.5 * seconds / max(t1, 1e-9) * cores)))
+    nv = int(max(cores, min(200000, 0.5 * seconds / max(t1v, 1e-9) * cores)))
     vsel = rng.choice(obs.nvis, size=min(nv, obs.nvis), replace=False)
     t0 = time.perf_counter()
     direct.degrid(obs.uvw, obs.freq, I, obs.pixsize_x, obs.pixsize_y, vis_index=vsel)
     td = time.perf_counter() - t0
     degrid_vps = len(vsel) / td                      # visibilities degridded per second
     # grid: one pixel costs nvis terms
-    t0 = time.perf_counter()
-    direct.grid(obs.uvw, obs.freq, d, obs.npix_x, obs.npix_y, obs.pixsize_x, obs.pixsize_y,
-                pixel_index=np.array([0]), nthreads=1)
-    t1 = time.perf_counter() - t0
-    npx = int(max(cores, min(npix, 0.5 * seconds / max(t1, 1e-9) * cores)))
+    npx = int(max(cores, min(npix, 0.5 * seconds / max(t1p, 1e-9) * cores)))
     psel = rng.choice(npix, size=npx, replace=False)
     t0 = time.perf_counter()
     direct.grid(obs.uvw, obs.freq, d, obs.npix_x, obs.npix_y, obs.pixsize_x, obs.pixsize_y, pixel_index=psel)
@@ -165,8 +172,9 @@ def oracle_rate(obs, I, d, seconds):
     step_s = 2 * (obs.nvis / degrid_vps + obs.nvis / grid_vps)
     sample = (f"degrid of {len(vsel)} sampled visibilities against all {nnz} nonzero pixels "
               f"({td:.1f} s) and grid of {len(psel)} sampled pixels over all {obs.nvis} "
-              f"visibilities ({tg:.1f} s), extrapolated to the full workload")
-    return 4 * obs.nvis / step_s, cores, sample, step_s
+              f"visibilities ({tg:.1f} s) on {cores} threads, extrapolated to the full workload; "
+              f"one core: {len(v1)} visibilities and {len(p1)} pixels, extrapolated")
+    return 4 * obs.nvis / step_s, cores, sample, step_s, 4 * obs.nvis / step1
 
 
 def make_inputs(workload):
@@ -186,7 +194,7 @@ def run_reference(args):
     rates = []
     cores = sample = None
     for i in range(args.warmup + args.steps):
-        vps, cores, sample, _ = oracle_rate(obs, I, d, per_step)
+        vps, cores, sample, _, _ = oracle_rate(obs, I, d, per_step)
         if i >= args.warmup:
             rates.append(vps)
     value = statistics.median(rates)
@@ -397,6 +405,148 @@ def run_serve(args):
     return 0
 
 
+# ------------------------------------------------------------------------------------------
+# algorithmic bytes (scope-table accounting) and per-stage roofline fractions
+# ------------------------------------------------------------------------------------------
+STAGE_KEYS = {"screen": "ms_screen", "fft": "ms_fft", "gridding": "ms_grid", "accumulate": "ms_accum"}
+
+
+def bytes_8d(info, obs, prec, direction):
+    """Algorithmic HBM bytes of one operator call, per stage: every w-plane cell (b = 8 bytes in
+    FP32, 16 in FP64) is written once by the screen, read and written once by the plane FFT,
+    read once by the degridding, read and written once by the gridding, and read once by the
+    accumulation (k_plane = 4 for degrid, 5 for grid); the (de)gridding also moves the
+    visibilities (b each), a 4-byte index entry per visibility and the 24-byte uvw rows."""
+    b = 8 if prec == "f32" else 16
+    cells = info["nu"] * info["nv"] * info["nw"]
+    vis_b = obs.nvis * (b + 4) + obs.nrows * 24
+    if direction == "degrid":
+        return {"screen": cells * b, "fft": 2 * cells * b, "gridding": cells * b + vis_b}
+    return {"gridding": 2 * cells * b + vis_b, "fft": 2 * cells * b, "accumulate": cells * b}
+
+
+def stage_fractions(stats, info, obs, prec, direction, hbm_gbs):
+    """Per stage and for the whole call: algorithmic bytes / HBM peak / measured time."""
+    by = bytes_8d(info, obs, prec, direction)
+    out = {}
+    for st, nb in by.items():
+        ms = stats[STAGE_KEYS[st]]
+        out[st] = {"bytes": nb, "ms": round(ms, 4),
+                   "frac": (nb / (hbm_gbs * 1e9)) / (ms * 1e-3) if ms > 0 else None}
+    tot = sum(by.values())
+    out["call"] = {"bytes": tot, "ms": round(stats["ms_total"], 4),
+                   "frac": (tot / (hbm_gbs * 1e9)) / (stats["ms_total"] * 1e-3)}
+    return out
+
+
+def median_stats(sts):
+    return {k: statistics.median(s[k] for s in sts) for k in
+            ("ms_total", "ms_prep", "ms_screen", "ms_fft", "ms_grid", "ms_accum")}
+
+
+def make_plans(wg, obs, modes, dev, grid_variant=0):
+    """Resident plans per precision mode, with their creation time (the index build, the
+    per-pixel tables, the FFT set-up; wg_plan_create synchronises)."""
+    import torch
+    plans, plan_ms = {}, {}
+    for prec, eps in modes:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plans[prec] = wg.Plan(obs.uvw, obs.freq, obs.npix_x, obs.npix_y, obs.pixsize_x,
+                              obs.pixsize_y, eps, prec, device=dev, grid_variant=grid_variant)
+        plan_ms[prec] = (time.perf_counter() - t0) * 1e3
+    return plans, plan_ms
+
+
+def error_sample(obs, nv, npx, seed=0):
+    rng = np.random.default_rng(seed)
+    return (np.sort(rng.choice(obs.nvis, nv, replace=False)),
+            np.sort(rng.choice(obs.npix_x * obs.npix_y, npx, replace=False)))
+
+
+def gpu_samples(vout, gout, vsel, psel):
+    """The GPU outputs at the sampled visibilities / pixels (host numpy, complex128 / float64)."""
+    import torch
+    vi = torch.from_numpy(vsel).to(vout.device)
+    pi = torch.from_numpy(psel).to(gout.device)
+    return (vout.reshape(-1).index_select(0, vi).cpu().numpy().astype(np.complex128),
+            gout.reshape(-1).index_select(0, pi).cpu().numpy().astype(np.float64))
+
+
+def oracle_errors(obs, I, d, vsel, psel, samples):
+    """Relative L2 error (Sec. 5.2) of each mode's sampled GPU outputs against the FP64 oracle
+    evaluated at the same visibilities and pixels (part of the CPU-baseline leg)."""
+    from oracle import direct
+    direct.build()
+    t0 = time.perf_counter()
+    rv = direct.degrid(obs.uvw, obs.freq, I, obs.pixsize_x, obs.pixsize_y, vis_index=vsel)
+    ri = direct.grid(obs.uvw, obs.freq, d, obs.npix_x, obs.npix_y, obs.pixsize_x,
+                     obs.pixsize_y, pixel_index=psel)
+    t = time.perf_counter() - t0
+    errs = {m: {"degrid": direct.rel_l2(v, rv), "grid": direct.rel_l2(g, ri)}
+            for m, (v, g) in samples.items()}
+    return errs, (f"{len(vsel)} sampled visibilities and {len(psel)} sampled pixels against the "
+                  f"FP64 direct-sum oracle ({t:.1f} s on the host)")
+
+
+def run_config_1e8(args, wg, dev, hbm_gbs):
+    """The 1e8-visibility workload (8192^2 at 4 arcsec, 128 antennas x 193 times x 64 channels
+    truncated to 1e8 visibilities) at eps = 1e-5 FP32 and eps = 1e-12 FP64: plan creation time,
+    one warm-up and `steps` timed calls per direction with per-stage CUDA-event times, the
+    per-stage fractions of the HBM roofline by algorithmic bytes, and sampled GPU outputs for
+    the error against the oracle."""
+    import torch
+    from paper_2010_10122_gb300 import synthetic as S
+    modes8 = tuple(m for m in (("f32", 1e-5), ("f64", 1e-12)) if m[0] in args.modes_1e8.split(","))
+    t0 = time.perf_counter()
+    obs = S.wide_8k()
+    I = S.point_source_image(obs.npix_x, obs.npix_y, seed=0)
+    d = S.complex_normal((obs.nrows, obs.nchan), seed=1)
+    gen_s = time.perf_counter() - t0
+    vsel, psel = error_sample(obs, 128, 8, seed=2)
+    out = {"workload": "wide_8k", "nvis": obs.nvis, "npix": [obs.npix_x, obs.npix_y],
+           "pixsize_arcsec": obs.pixsize_x / S.ARCSEC, "uv_scale": obs.uv_scale,
+           "steps": args.steps_1e8, "warmup": 1, "input_generation_s": round(gen_s, 1),
+           "modes": {}}
+    samples = {}
+    for prec, eps in modes8:
+        rdt, cdt = (torch.float32, torch.complex64) if prec == "f32" else (torch.float64, torch.complex128)
+        plans, plan_ms = make_plans(wg, obs, ((prec, eps),), dev)
+        p = plans[prec]
+        din = torch.from_numpy(I).to(dev, rdt)
+        vin = torch.from_numpy(d).to(dev, cdt)
+        vout = torch.empty((obs.nrows, obs.nchan), dtype=cdt, device=dev)
+        gout = torch.empty((obs.npix_x, obs.npix_y), dtype=rdt, device=dev)
+        p.degrid(din, out=vout)
+        p.grid(vin, out=gout)
+        torch.cuda.synchronize()
+        sts = {"degrid": [], "grid": []}
+        for _ in range(args.steps_1e8):
+            sts["degrid"].append(p.degrid(din, out=vout, stats=True)[1])
+            sts["grid"].append(p.grid(vin, out=gout, stats=True)[1])
+        torch.cuda.synchronize()
+        info = p.info
+        m = {"eps": eps, "alpha": info["alpha"], "sigma": info["sigma"],
+             "uv_grid": [info["nu"], info["nv"]], "nw": info["nw"], "batch": info["batch"],
+             "fft": FFT_NAMES[info["fft_impl"]], "err_model": info["err_model"],
+             "plan_ms": round(plan_ms[prec], 1),
+             "index_bytes_per_vis": info["index_bytes"] / max(1, obs.nvis)}
+        for direction in ("degrid", "grid"):
+            med = median_stats(sts[direction])
+            m[direction] = {"vis_per_s": obs.nvis / (med["ms_total"] * 1e-3),
+                            **{k: round(v, 3) for k, v in med.items()},
+                            "hbm_roofline": stage_fractions(med, info, obs, prec, direction, hbm_gbs)}
+        out["modes"][f"{prec}_eps{eps:g}"] = m
+        samples[f"{prec}_eps{eps:g}"] = gpu_samples(vout, gout, vsel, psel)
+        p.close()
+        del din, vin, vout, gout
+        torch.cuda.empty_cache()
+    tm = {k: mm["degrid"]["ms_total"] + mm["grid"]["ms_total"] for k, mm in out["modes"].items()}
+    if "f64_eps1e-12" in tm and "f32_eps1e-05" in tm:
+        out["fp32_vs_fp64_speedup"] = tm["f64_eps1e-12"] / tm["f32_eps1e-05"]
+    return out, (obs, I, d, vsel, psel, samples)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -423,11 +573,10 @@ def main():
     obs, I, d = make_inputs(args.workload)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    plans, dins, vins, vouts, gouts = {}, {}, {}, {}, {}
+    plans, plan_ms = make_plans(wg, obs, MODES, dev, args.grid_variant)
+    dins, vins, vouts, gouts = {}, {}, {}, {}
     for prec, eps in MODES:
         rdt, cdt = (torch.float32, torch.complex64) if prec == "f32" else (torch.float64, torch.complex128)
-        plans[prec] = wg.Plan(obs.uvw, obs.freq, obs.npix_x, obs.npix_y, obs.pixsize_x, obs.pixsize_y,
-                              eps, prec, device=dev, grid_variant=args.grid_variant)
         dins[prec] = torch.from_numpy(I).to(dev, rdt)
         vins[prec] = torch.from_numpy(d).to(dev, cdt)
         vouts[prec] = torch.empty((obs.nrows, obs.nchan), dtype=cdt, device=dev)
@@ -494,32 +643,39 @@ def main():
         for p in plans.values():
             p.close()
         return 0
-    modes = {}
-    launches = 0
-    for prec, eps in MODES:
-        info = plans[prec].info
-        m = {"eps": eps, "alpha": info["alpha"], "sigma": info["sigma"],
-             "uv_grid": [info["nu"], info["nv"]], "nw": info["nw"], "batch": info["batch"],
-             "fft": FFT_NAMES[info["fft_impl"]], "err_model": info["err_model"]}
-        for direction in ("degrid", "grid"):
-            sts = per_call[(prec, direction)]
-            med = {k: statistics.median(s[k] for s in sts) for k in
-                   ("ms_total", "ms_prep", "ms_screen", "ms_fft", "ms_grid", "ms_accum")}
-            m[direction] = {"vis_per_s": obs.nvis / (med["ms_total"] * 1e-3),
-                            **{k: round(v, 4) for k, v in med.items()}}
-            launches += sts[-1]["n_kernels"]
-        modes[f"{prec}_eps{eps:g}"] = m
-    tm = {k: m["degrid"]["ms_total"] + m["grid"]["ms_total"] for k, m in modes.items()}
-    speedup = (tm["f64_eps1e-12"] / tm["f32_eps1e-05"]
-               if "f64_eps1e-12" in tm and "f32_eps1e-05" in tm else None)
 
-    # ---- roofline of the dominant library kernel ----------------------------------------------
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    fp32_meas = wg.fma_peak("f32")     # flop/s, an FMA = 2 (measured now, on this GPU)
+    fp64_meas = wg.fma_peak("f64")
+
+    modes = {}
+    launches = 0
+    step_bytes = 0
+    for prec, eps in MODES:
+        info = plans[prec].info
+        m = {"eps": eps, "alpha": info["alpha"], "sigma": info["sigma"],
+             "uv_grid": [info["nu"], info["nv"]], "nw": info["nw"], "batch": info["batch"],
+             "fft": FFT_NAMES[info["fft_impl"]], "err_model": info["err_model"],
+             "plan_ms": round(plan_ms[prec], 2),
+             "index_bytes_per_vis": info["index_bytes"] / max(1, obs.nvis)}
+        for direction in ("degrid", "grid"):
+            med = median_stats(per_call[(prec, direction)])
+            hr = stage_fractions(med, info, obs, prec, direction, hbm_peak)
+            step_bytes += hr["call"]["bytes"]
+            m[direction] = {"vis_per_s": obs.nvis / (med["ms_total"] * 1e-3),
+                            **{k: round(v, 4) for k, v in med.items()}, "hbm_roofline": hr}
+            launches += per_call[(prec, direction)][-1]["n_kernels"]
+        modes[f"{prec}_eps{eps:g}"] = m
+    tm = {k: m["degrid"]["ms_total"] + m["grid"]["ms_total"] for k, m in modes.items()}
+    speedup = (tm["f64_eps1e-12"] / tm["f32_eps1e-05"]
+               if "f64_eps1e-12" in tm and "f32_eps1e-05" in tm else None)
+
+    # ---- roofline of the dominant library kernel ----------------------------------------------
     stage_ms = {}
     for prec, _ in MODES:
         k = f"{prec}_eps{dict(MODES)[prec]:g}"
@@ -533,6 +689,11 @@ def main():
     dom = max(stage_ms, key=stage_ms.get)
     prec_d, dir_d, stage_d = dom
     info_d = plans[prec_d].info
+    hbm_d = modes[f"{prec_d}_eps{dict(MODES)[prec_d]:g}"][dir_d]["hbm_roofline"][stage_d]
+    hbm_8d = {"bytes": hbm_d["bytes"], "achieved_gbs": hbm_d["bytes"] / (stage_ms[dom] * 1e-3) / 1e9,
+              "peak_gbs": hbm_peak, "frac": hbm_d["frac"],
+              "accounting": "w-plane cells x bytes per cell x passes (screen 1, FFT 2, degrid 1, "
+                            "grid 2, accumulate 1) + visibility data"}
     roof = None
     if stage_d == "fft":
         # double-float plane FFT: FP32-ALU (issue) bound; work = its FP32 arithmetic
@@ -548,31 +709,32 @@ def main():
                 "algorithmic_bytes": abytes,
                 "peak_source": "FP32 arithmetic instructions/s: 152 SMs x 128 lanes x 2.07 GHz "
                                "(an FMA counts once)",
-                "stage": f"{prec_d} {dir_d}"}
+                "peak_measured": fp32_meas / 2 / 1e12, "frac_measured": ach / (fp32_meas / 2),
+                "peak_measured_source": "wg_fma_peak(WG_F32) on this GPU now: FMA instructions/s",
+                "stage": f"{prec_d} {dir_d}", "hbm_8d": hbm_8d}
     elif stage_d == "gridding" and prec_d == "f64":
         flops = algorithmic_flops_per_vis(info_d["alpha"]) * plans[prec_d].info["nvis"]
         peak = 1.25e12   # FP64 FMA pipe: nominal GB300 rate (152 SMs x 2 FMA/clk x 2 x 2.07 GHz)
         ach = flops / (stage_ms[dom] * 1e-3)
         roof = {"bound": "alu", "kernel": f"k_{dir_d}<double,16>", "achieved": ach / 1e12,
                 "peak": peak / 1e12, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-                "peak_source": "nominal FP64 FMA rate (unit counts x clock); probe measured 1.19"}
+                "peak_measured": fp64_meas / 1e12, "frac_measured": ach / fp64_meas,
+                "stage": f"{prec_d} {dir_d}", "hbm_8d": hbm_8d}
     else:
-        # plane-traffic kernels: bytes the stage must move per batch of planes
-        b = 8 if prec_d == "f32" else 16
-        cells = info_d["nu"] * info_d["nv"] * info_d["nw"]
-        npix = obs.npix_x * obs.npix_y
-        if stage_d == "screen":
-            byts = cells * b + npix * (16 if prec_d == "f32" else 32)
-        elif stage_d == "accumulate":
-            byts = info_d["nw"] * npix * b + npix * 8 * 2
-        else:
-            byts = cells * b
-        ach = byts / (stage_ms[dom] * 1e-3)
-        roof = {"bound": "hbm", "kernel": f"{stage_d} ({prec_d}, {dir_d})", "achieved": ach / 1e9,
-                "peak": hbm_peak, "unit": "GB/s", "frac": ach / 1e9 / hbm_peak, "traffic": None}
+        roof = {"bound": "hbm", "kernel": f"{stage_d} ({prec_d}, {dir_d})",
+                "achieved": hbm_8d["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
+                "frac": hbm_d["frac"], "traffic": None, "stage": f"{prec_d} {dir_d}",
+                "hbm_8d": hbm_8d}
+    step_roof = {"bytes": step_bytes, "achieved_gbs": step_bytes / (ms_per_step * 1e-3) / 1e9,
+                 "peak_gbs": hbm_peak, "frac": step_bytes / (hbm_peak * 1e9) / (ms_per_step * 1e-3)}
+
+    # sampled outputs of the headline workload for the error against the oracle (CPU leg)
+    vsel2, psel2 = error_sample(obs, 256, 96, seed=0)
+    samples2 = {f"{prec}_eps{eps:g}": gpu_samples(vouts[prec], gouts[prec], vsel2, psel2)
+                for prec, eps in MODES}
 
     # ---- end to end: host buffers, copies inside the timed region ------------------------------
-    e2e = None
+    e2e = e2e_one = None
     if not args.no_e2e:
         h_in = {}
         for prec, _ in MODES:
@@ -606,10 +768,51 @@ def main():
         e2e = {"value": ws * ncalls * obs.nvis / (tot / args.steps * 1e-3), "unit": "vis/s",
                "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
 
+        # one-shot calls (the paper's dirty2ms / ms2dirty, App. B): plan creation -- index
+        # build, tables, FFT set-up -- inside every call, from host buffers
+        uvw_h = torch.from_numpy(obs.uvw).pin_memory()
+        freq_h = torch.from_numpy(obs.freq)
+
+        def oneshot_step():
+            for prec, eps in MODES:
+                vo = wg.dirty2ms(uvw_h, freq_h, h_in[prec][0], pixsize_x=obs.pixsize_x,
+                                 pixsize_y=obs.pixsize_y, epsilon=eps, device=dev)
+                go = wg.ms2dirty(uvw_h, freq_h, h_in[prec][1], npix_x=obs.npix_x,
+                                 npix_y=obs.npix_y, pixsize_x=obs.pixsize_x,
+                                 pixsize_y=obs.pixsize_y, epsilon=eps, device=dev)
+                h_out[prec][0].copy_(vo, non_blocking=True)
+                h_out[prec][1].copy_(go, non_blocking=True)
+        oneshot_step()
+        torch.cuda.synchronize()
+        n1 = max(1, min(3, args.steps))
+        t0 = time.perf_counter()
+        for _ in range(n1):
+            oneshot_step()
+        torch.cuda.synchronize()
+        t1 = (time.perf_counter() - t0) / n1
+        e2e_one = {"value": ncalls * obs.nvis / t1, "unit": "vis/s", "steps": n1,
+                   "timing": "host wall clock (plan creation synchronises the stream)",
+                   "h2d_bytes_per_step": bi + len(MODES) * 2 * uvw_h.numel() * 8,
+                   "d2h_bytes_per_step": bo}
+
+    # ---- the 1e8-visibility workload ---------------------------------------------------------
+    cfg8 = ctx8 = None
+    if args.modes_1e8 and ws == 1 and args.workload != "wide_8k":
+        cfg8, ctx8 = run_config_1e8(args, wg, dev, hbm_peak)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        vps, cores, sample, _ = oracle_rate(obs, I, d, args.oracle_seconds)
-        cpu = {"value": vps, "unit": "vis/s", "cores": cores, "kind": "oracle", "sample": sample}
+        vps, cores, sample, _, vps1 = oracle_rate(obs, I, d, args.oracle_seconds)
+        cpu = {"value": vps, "unit": "vis/s", "cores": cores, "kind": "oracle", "sample": sample,
+               "value_1core": vps1}
+        errs, how = oracle_errors(obs, I, d, vsel2, psel2, samples2)
+        for k, e in errs.items():
+            modes[k]["rel_l2_err"] = {**e, "sample": how}
+        if cfg8 is not None:
+            o8, I8, d8, vs8, ps8, smp8 = ctx8
+            errs8, how8 = oracle_errors(o8, I8, d8, vs8, ps8, smp8)
+            for k, e in errs8.items():
+                cfg8["modes"][k]["rel_l2_err"] = {**e, "sample": how8}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "vis/s", "n_gpus": ws,
@@ -624,7 +827,12 @@ def main():
                            "parallelism": f"replicas{ws}" if ws > 1 else "single",
                            "l2": "flushed between steps (256 MiB write)"},
                 "modes": modes, "fp32_vs_fp64_speedup": speedup,
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roof, "step_hbm_roofline": step_roof,
+                "peaks": {"hbm_gbs": hbm_peak, "hbm_source": "MEASURED_PEAKS.json",
+                          "fp32_fma_tflops_measured": fp32_meas / 1e12,
+                          "fp64_fma_tflops_measured": fp64_meas / 1e12},
+                "cpu_baseline": cpu, "e2e": e2e, "e2e_oneshot": e2e_one,
+                "config_1e8": cfg8,
                 "gpu_launches": launches * args.steps, "clocks": clk}
         print(json.dumps(line), flush=True)
     for p in plans.values():

@@ -23,9 +23,15 @@
  *    m = (jy - npix_y/2) * pixsize_y (Sec. 2, sets L and M); x pairs with u.
  *  - vis:   (nrows, nchan) complex, interleaved (re, im).
  *  - Precision (App. B: the data type selects the precision): WG_F32 uses float / complex64
- *    buffers and FP32 gridding arithmetic; WG_F64 uses double / complex128 and FP64
- *    throughout.  Coordinates, plane indices and w-screen phases are formed in FP64 in
- *    both modes.
+ *    buffers, FP32 uv planes, FP32 (de)gridding and FP32 plane FFTs; WG_F64 uses double /
+ *    complex128 buffers and an FP64-accurate pipeline, whose uv planes, plane FFTs and
+ *    (de)gridding sums run either in FP64 (fft_impl 1 or 3) or, with the library's
+ *    double-float FFT (fft_impl 2, the usual automatic choice), in double-float pair
+ *    arithmetic on the FP32 pipes (a pair of floats, ~48-bit significand, unit roundoff
+ *    2^-47); the planner sizes sigma so that this rounding stays inside epsilon.  Both modes
+ *    form coordinates, plane indices and the per-visibility w-reference phase in FP64 and
+ *    accumulate the gridded image in FP64.  The per-plane w-screen phase is FP64 in WG_F64;
+ *    WG_F32 reduces it exactly in FP32 (a 13-bit split of Delta w (n - 1)) before sincospif.
  *  - wgt:   optional (nrows, nchan) real weights of the buffer precision; multiplies the
  *    degrid output and the grid input (App. B).  NULL = all ones.
  *  - mask:  optional (nrows, nchan) uint8; visibilities with mask == 0 are not processed
@@ -52,7 +58,7 @@ enum wg_status {
   WG_ERR_OOM = 2,     /* device allocation failed or exceeds the workspace cap */
   WG_ERR_CUDA = 3,    /* a CUDA runtime call failed (message has the CUDA error string) */
   WG_ERR_CUFFT = 4,   /* a cuFFT call failed */
-  WG_ERR_TIMEOUT = 5, /* a bounded host wait on device work ran out */
+  WG_ERR_TIMEOUT = 5, /* a bounded host wait on device work ran out (wg_wait) */
   WG_ERR_INTERNAL = 6 /* a device-side consistency check failed (e.g. plane index out of range) */
 };
 
@@ -60,9 +66,10 @@ enum wg_precision { WG_F32 = 0, WG_F64 = 1 };
 
 /* Opaque plan: geometry, kernel choice and the on-device visibility index for one set of
  * (uvw, freq, mask, image geometry, epsilon, precision).  Reusable for any number of
- * degrid / grid calls.  The plan's device data is read-only after creation and every call
- * allocates its own workspace, so calls on one plan may run concurrently on different
- * streams (host threads included); destroy the plan only after its calls have finished. */
+ * degrid / grid calls.  The plan's device data is read-only after creation and every
+ * wg_degrid / wg_grid call allocates its own workspace, so those calls on one plan may run
+ * concurrently on different streams (host threads included).  wg_plan_destroy waits for all
+ * work on the plan's device before it frees the plan. */
 typedef struct wg_plan wg_plan;
 
 /* Options for wg_plan_create (zero-initialise, then set what you need). */
@@ -88,7 +95,9 @@ typedef struct wg_options {
   int fft_impl;            /* plane FFTs: 0 = automatic (WG_F32: cuFFT C2C; WG_F64: the
                               cheaper of 2 and 3 whose predicted error fits epsilon),
                               1 = cuFFT 2-D, 2 = the library's double-float FFT (WG_F64 only,
-                              grid sides <= 6400; its ~5e-15 rounding is amplified by the
+                              grid sides up to 6400 with prime factors 2, 3, 5, 7, 11, and
+                              sides up to 25600 that are 2 or 4 times such a side (each line
+                              then runs on 2 or 4 CTAs); its ~5e-15 rounding is amplified by the
                               1 / psi correction, so the planner may raise sigma for it; the
                               uv planes are then kept as double-float pairs and (de)gridded in
                               pair arithmetic),
@@ -163,7 +172,8 @@ int wg_plan_create(const double* uvw, const double* freq, int64_t nrows, int64_t
                    double epsilon, int precision, const uint8_t* mask,
                    const wg_options* opt, void* stream, wg_plan** out);
 
-/* Release a plan and its device memory (after synchronising the plan's last stream). */
+/* Release a plan and its device memory.  Synchronises the plan's device first (every stream
+ * on it, so calls still in flight on any stream finish before their index memory is freed). */
 int wg_plan_destroy(wg_plan* plan);
 
 /* Copy the plan parameters into *info (host call, no device work). */
@@ -196,9 +206,11 @@ int wg_degrid(wg_plan* plan, const void* dirty, const void* wgt, void* vis, void
  * library holds until the process exits.  Nothing in it has to start at zero.  This call makes
  * no cudaMalloc / cudaFree or other allocating call; the plan's cuFFT handles run on the
  * scratch through cufftSetWorkArea.
- *   The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  The plan's device
- * must be current.
+ *   The array's device address is looked up (cudaGetSymbolAddress, once per device) by
+ * wg_plan_create, for plans whose per-call workspace fits the array, with the plan's device
+ * current.  Under CUDA's lazy module loading that lookup is when the runtime loads the module
+ * that holds the array and allocates its 64 MiB, so create such plans during set-up, where
+ * allocation is allowed, and before any stream capture.  The plan's device must be current.
  *   All calls share the one array and it keeps the last call's contents: calls whose work
  * overlaps on the GPU (other streams, other threads, other plans) race and corrupt each
  * other's results; order them on one stream or synchronise between them.
@@ -232,6 +244,13 @@ int wg_ms2dirty(const double* uvw, const double* freq, int64_t nrows, int64_t nc
                 const void* vis, const void* wgt, int64_t npix_x, int64_t npix_y,
                 double pixsize_x, double pixsize_y, double epsilon, int precision,
                 int do_wstacking, const uint8_t* mask, void* dirty, void* stream);
+
+/* Bounded host wait: returns WG_OK once all work enqueued on `stream` (void* cudaStream_t,
+ * NULL = legacy default stream) so far has finished, WG_ERR_TIMEOUT if it has not finished
+ * after timeout_ms milliseconds (the work keeps running; call again or give up on it), or
+ * WG_ERR_CUDA if the stream reports an error.  timeout_ms < 0 waits without bound.  Polls
+ * cudaStreamQuery with short sleeps; launches nothing. */
+int wg_wait(void* stream, double timeout_ms);
 
 /* Message of the last failing call on this thread ("" if none). Never NULL. */
 const char* wg_last_error(void);
@@ -291,6 +310,13 @@ int wg_fft_time(int64_t n, int precision, int64_t batch, int reps, int impl, dou
  * transform on each call (a utility, not a hot path); synchronises `stream`. */
 int wg_fft2d(void* data, int64_t nu, int64_t nv, int64_t batch, int precision, int impl, int sign,
              void* stream);
+
+/* Arithmetic peak of the current device: FP32 (precision WG_F32) or FP64 (WG_F64) fused
+ * multiply-add throughput in flop/s (an FMA counts 2), the best of five timed launches of
+ * independent FMA chains on every SM (CUDA events, after a warm-up launch).  The roofline
+ * denominator of the library's ALU-bound kernels.  Allocates and frees a small output buffer;
+ * synchronises the device.  Errors: WG_ERR_ARG, WG_ERR_OOM, WG_ERR_CUDA. */
+int wg_fma_peak(int precision, double* flops_per_s);
 
 /* Library version string. */
 const char* wg_version(void);

@@ -11,8 +11,8 @@
  *           and n = sqrt(1 - l^2 - m^2) (Sec. 2, below Eq. 1);
  *
  *   grid    (R0^dagger d)_lm = Re sum_k exp(+2 pi i [u_k l + v_k m - w_k (n_lm - 1)]) d_k / n_lm
- *           the direct adjoint used as the accuracy reference in Sec. 6.2; the real
- *           part is taken because R maps a real image to complex data (Sec. 6.1,
+ *           the direct adjoint used as the accuracy reference in Sec. 5.2; the real
+ *           part is taken because R maps a real image to complex data (Sec. 5.1,
  *           Eq. adjointness).
  *
  * Effective coordinates: u = u~ * f / c (and likewise v, w), Sec. 2 (u := u~ (x) 1/lambda).

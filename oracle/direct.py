@@ -1,4 +1,4 @@
-"""Direct-sum FP64 oracle for degrid (Eq. rime) and grid (its direct adjoint, Sec. 6.2).
+"""Direct-sum FP64 oracle for degrid (Eq. rime) and grid (its direct adjoint, Sec. 5.2).
 
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
 ``bench.py``'s ``cpu_baseline`` / ``--impl reference`` legs may import this module.
@@ -129,13 +129,13 @@ def threads_used(nthreads=0):
 
 
 def rel_l2(x, ref):
-    """Relative L2 error ||x - ref|| / ||ref|| (Sec. 6.2, eps_rms)."""
+    """Relative L2 error ||x - ref|| / ||ref|| (Sec. 5.2, eps_rms)."""
     x = np.asarray(x); ref = np.asarray(ref)
     return float(np.linalg.norm((x - ref).ravel()) / np.linalg.norm(ref.ravel()))
 
 
 def adjointness_error(I, RI, d, Rd):
-    """eps_adj of Sec. 6.1: |Re<R I, d> - <I, R^dagger d>| / min(|d||R I|, |I||R^dagger d|)."""
+    """eps_adj of Sec. 5.1: |Re<R I, d> - <I, R^dagger d>| / min(|d||R I|, |I||R^dagger d|)."""
     I = np.asarray(I, dtype=np.float64).ravel(); Rd = np.asarray(Rd, dtype=np.float64).ravel()
     RI = np.asarray(RI, dtype=np.complex128).ravel(); d = np.asarray(d, dtype=np.complex128).ravel()
     lhs = np.real(np.vdot(RI, d))

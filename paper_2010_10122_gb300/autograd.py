@@ -2,7 +2,7 @@
 
 R maps a real image to complex visibilities and is R-linear (Sec. 2: "R is an R-linear map");
 its adjoint with respect to the real inner product on images and Re<.,.> on visibilities
-(Sec. 6.1, Eq. adjointness) is R^dagger = grid.  PyTorch hands a complex output's backward
+(Sec. 5.1, Eq. adjointness) is R^dagger = grid.  PyTorch hands a complex output's backward
 the gradient dL/dRe(y) + i dL/dIm(y); for y = R x with real x the chain rule gives
 dL/dx = Re(R^H g) = R^dagger(g), so the backward of degrid is one grid call, and the backward of
 grid is one degrid call.  Neither Function keeps activations: only the plan (resident) and the

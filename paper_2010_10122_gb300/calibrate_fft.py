@@ -3,8 +3,10 @@ to csrc/fft_table.inc (run on the target GPU; the library must be built).
 
 Candidates: n = 32 m for 4 <= m <= 512 with m 11-smooth (FFT-friendly multiples of the uv
 tile).  For each n the batched 2-D C2C (FP32) and Z2Z (FP64) cuFFT transforms and the library's
-double-float FFT (FP64 planes, sides up to 6400) are timed through the library's wg_fft_time
-entry point with ~1-2 GiB of planes per batch.  The planner uses the
+double-float FFT (FP64 planes; sizes it does not support get 0) are timed through the library's
+wg_fft_time entry point with ~1-2 GiB of planes per batch.  --columns re-measures only some of
+the three columns (c2c, z2z, df64) and --min-n only sizes from there on, keeping the other
+entries of the existing table.  The planner uses the
 table to pick, for each oversampling factor, the fastest size >= sigma * n and to price the
 FFT stage in its cost model (Sec. 4.1).
 
@@ -26,9 +28,19 @@ def smooth(m, primes=(2, 3, 5, 7, 11)):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--max-n", type=int, default=16384)
+    ap.add_argument("--min-n", type=int, default=0)
+    ap.add_argument("--columns", default="c2c,z2z,df64")
     ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)),
                                                   "csrc", "fft_table.inc"))
     args = ap.parse_args()
+    cols = args.columns.split(",")
+    old = {}
+    if os.path.exists(args.out):
+        for ln in open(args.out):
+            ln = ln.strip()
+            if ln.startswith("{"):
+                v = [float(x) for x in ln.strip("{},").split(",")]
+                old[int(v[0])] = v[1:]
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     from paper_2010_10122_gb300 import _build
     _build.build()
@@ -41,13 +53,17 @@ def main():
             continue
         n = 32 * m
         out = [n]
-        for prec, b, impl in (("f32", 8, 1), ("f64", 16, 1), ("f64", 16, 2)):
-            if impl == 2 and n > 6400:
-                out.append(0.0)
+        for c, (prec, b, impl) in enumerate((("f32", 8, 1), ("f64", 16, 1), ("f64", 16, 2))):
+            name = ("c2c", "z2z", "df64")[c]
+            if (name not in cols or n < args.min_n) and n in old:
+                out.append(old[n][c])
                 continue
             batch = max(1, min(64, int((1.5 * 2**30) // (n * n * b))))
             reps = 3 if n * n * b * batch > 2**28 else 6
-            out.append(wg.fft_time(n, prec, batch=batch, reps=reps, impl=impl))
+            try:
+                out.append(wg.fft_time(n, prec, batch=batch, reps=reps, impl=impl))
+            except wg.WgridError:   # a size this implementation does not support
+                out.append(0.0)
         rows.append(out)
         print(f"n={n:6d} c2c {out[1]*1e3:9.2f} us/plane  z2z {out[2]*1e3:10.2f} us/plane  "
               f"df64 {out[3]*1e3:10.2f} us/plane", flush=True)

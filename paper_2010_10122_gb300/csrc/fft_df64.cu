@@ -38,11 +38,17 @@ struct DftConst {
 
 constexpr int kMaxStages = 24;
 struct FftLine {
-  int n;                     // transform length
+  int n;                     // transform length held by one CTA (half the line when split)
   int nst;                   // number of radix stages
   int threads;               // CTA size of the line kernel (about n / 8)
   int radix[kMaxStages];
   const float4* tw;          // e^{-2 pi i t / n}, t = 0 .. n - 1, df64
+  // split lines (length S n, S = split = 2 or 4, too long for one CTA's shared memory): CTA h
+  // (h < S) of a line transforms y_h[j] = e^{-/+ 2 pi i j h / (S n)} sum_{r < S} x[j + r n]
+  // e^{-/+ 2 pi i r h / S}, one radix-S decimation-in-frequency step applied while loading,
+  // and its n outputs are the line's outputs S k + h.  split = 1: one CTA per line.
+  int split;
+  const float4* tw2;         // e^{-2 pi i t / (S n)}, t = 0 .. S n - 1, df64 (split lines only)
   DftConst k;
 };
 
@@ -193,18 +199,21 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // line per CTA).  kAll
 // adds the rare radices 2, 7 and 11, kept out of the common instance so that its register
 // allocation is not burdened with them.
-template <int TMAX, int MINB, bool kAll, bool kAsync>
+template <int TMAX, int MINB, bool kAll, bool kAsync, bool kSplit>
 __global__ void __launch_bounds__(TMAX, MINB)
 k_fft_lines(const __grid_constant__ FftLine L, void* __restrict__ data, int64_t plane_elems,
             int lines_per_plane, int64_t line_stride, int64_t elem_stride, int mode, int fwd,
             int split, int skip, int lhalf, int shalf, int64_t nlines) {
   extern __shared__ __align__(16) float4 fsm[];
   const int n = L.n;
+  const int S = kSplit ? L.split : 1;      // CTAs per line
+  const int nfull = S * n;                 // elements of the whole line
   const int T = blockDim.x;
   const int swz = (n & 7) == 0 ? 7 : 0;
   float4* src = fsm;
   float4* dst = fsm + n;
   auto line_base = [&](int64_t gl) -> int64_t {
+    gl /= S;                               // S CTAs per line, h = gl mod S
     const int64_t plane = gl / lines_per_plane;
     int line = (int)(gl - plane * lines_per_plane);
     if (line >= split) line += skip;
@@ -214,9 +223,45 @@ k_fft_lines(const __grid_constant__ FftLine L, void* __restrict__ data, int64_t 
   // written directly.  kAsync (pairs, modes 1 and 2): asynchronous copies, completed by the
   // thread's cp_async_wait_all.  Otherwise loaded kLoadBatch at a time through registers, doubles
   // (mode 0) split into float pairs on the way.
+  // element i of the whole line as a df64 complex value (0 in the known-zero range)
+  auto load_elem = [&](const float4* g4, int64_t base, int i) -> cdd {
+    if (i >= lhalf && i < nfull - lhalf) {
+      cdd z; z.r = dd_make(0.f, 0.f); z.i = z.r;
+      return z;
+    }
+    const float4 v = g4[base + (int64_t)i * elem_stride];
+    if (mode == 0) {
+      const double2 d = make_double2(__hiloint2double(__float_as_int(v.y), __float_as_int(v.x)),
+                                     __hiloint2double(__float_as_int(v.w), __float_as_int(v.z)));
+      cdd x; x.r = split_double(d.x); x.i = split_double(d.y);
+      return x;
+    }
+    return load_cdd(v);
+  };
   auto issue = [&](int64_t gl, float4* b) {
     const int64_t base = line_base(gl);
     const float4* g4 = reinterpret_cast<const float4*>(data);
+    if constexpr (kSplit) {   // the decimation step of this CTA's part (see FftLine)
+      const int h = (int)(gl % S);
+      const bool f = fwd != 0;
+#pragma unroll 2
+      for (int j = threadIdx.x; j < n; j += T) {
+        cdd x4[4];
+        if (S == 2) {
+          x4[0] = load_elem(g4, base, j);
+          x4[1] = load_elem(g4, base, j + n);
+          dft2(x4);
+        } else {
+#pragma unroll
+          for (int r = 0; r < 4; ++r) x4[r] = load_elem(g4, base, j + r * n);
+          dft4(x4, f);
+        }
+        cdd y = x4[h];
+        if (h > 0) y = c_mul(y, twiddle(L.tw2, j * h, f));
+        b[swizzle(j, swz)] = store_cdd(y);
+      }
+      return;
+    }
     if (kAsync) {
       for (int i = threadIdx.x; i < n; i += T) {
         float4* d = b + swizzle(i, swz);
@@ -274,28 +319,34 @@ k_fft_lines(const __grid_constant__ FftLine L, void* __restrict__ data, int64_t 
       Ns *= R;
     }
   };
-  auto store_line = [&](int64_t base) {
+  // result element i of this CTA is element i (or, split, 2 i + h) of the line
+  auto store_line = [&](int64_t gl) {
+    const int64_t base = line_base(gl);
+    const int h = (int)(gl % S), st = S;
     if (mode != 1) {
       float4* out = reinterpret_cast<float4*>(data) + base;
-      for (int i = threadIdx.x; i < n; i += T)
-        if (i < shalf || i >= n - shalf) out[i * elem_stride] = src[swizzle(i, swz)];
+      for (int i = threadIdx.x; i < n; i += T) {
+        const int o = st * i + h;
+        if (o < shalf || o >= nfull - shalf) out[(int64_t)o * elem_stride] = src[swizzle(i, swz)];
+      }
     } else {
       double2* out = reinterpret_cast<double2*>(data) + base;
       for (int i = threadIdx.x; i < n; i += T) {
-        if (i >= shalf && i < n - shalf) continue;   // not needed downstream
+        const int o = st * i + h;
+        if (o >= shalf && o < nfull - shalf) continue;   // not needed downstream
         cdd x = load_cdd(src[swizzle(i, swz)]);
         double2 v; v.x = join_double(x.r); v.y = join_double(x.i);
-        out[i * elem_stride] = v;
+        out[(int64_t)o * elem_stride] = v;
       }
     }
   };
   int64_t gl = blockIdx.x;
   if (gl >= nlines) return;
-  if constexpr (!kAsync) {   // one line per CTA
+  if constexpr (!kAsync) {   // one line (or half line) per CTA
     issue(gl, src);
     __syncthreads();
     run_stages();
-    store_line(line_base(gl));
+    store_line(gl);
     return;
   }
   issue(gl, src);
@@ -308,7 +359,7 @@ k_fft_lines(const __grid_constant__ FftLine L, void* __restrict__ data, int64_t 
     const int64_t gn = gl + gridDim.x;
     const bool more = gn < nlines;
     if (more) issue(gn, dst);
-    store_line(line_base(gl));
+    store_line(gl);
     if (!more) break;
     cp_async_wait_all();
     __syncthreads();   // the next line is in place everywhere, and src is no longer read
@@ -330,35 +381,49 @@ static dd host_dd(long double v) {
 struct Df64Fft {
   int nu = 0, nv = 0;
   FftLine lu, lv;
-  float4* tw_u = nullptr;
+  float4* tw_u = nullptr;   // line twiddles, then (split lines) the decimation twiddles
   float4* tw_v = nullptr;
 };
 
-// Two lines of n df64 complex values in shared memory per CTA (two CTAs per SM up to n = 3584).
+// Two lines of n df64 complex values in shared memory per CTA (two CTAs per SM up to n = 3584);
+// longer lines (up to kDf64MaxSplitSide) are split over two or four CTAs.
 static constexpr int64_t kMaxSide = kDf64MaxSide;
 
 bool df64_fft_supported(int64_t nu, int64_t nv) { return df64_side_ok(nu) && df64_side_ok(nv); }
 
-static cudaError_t make_line(int n, FftLine* L, float4** tw) {
+// e^{-2 pi i t / len} for t = 0 .. count - 1 as df64 (float4: re hi, re lo, im hi, im lo)
+static void twiddles(int len, int count, float4* h) {
+  const long double two_pi = 6.283185307179586476925286766559L;
+  for (int t = 0; t < count; ++t) {
+    long double a = two_pi * (long double)t / (long double)len;
+    dd c = host_dd(cosl(a)), s = host_dd(-sinl(a));
+    h[t] = make_float4(c.h, c.l, s.h, s.l);
+  }
+}
+
+static cudaError_t make_line(int nline, FftLine* L, float4** tw) {
   std::memset(L, 0, sizeof(*L));
+  const int S = df64_line_split(nline);
+  if (S == 0) return cudaErrorInvalidValue;
+  const int n = nline / S;
   L->n = n;
+  L->split = S;
   Df64LinePlan lp;
   if (!df64_line_plan(n, &lp) || lp.nst > kMaxStages) return cudaErrorInvalidValue;
   L->nst = lp.nst;
   L->threads = lp.threads;
   for (int i = 0; i < lp.nst; ++i) L->radix[i] = lp.radix[i];
-  std::vector<float4> h(n);
-  const long double two_pi = 6.283185307179586476925286766559L;
-  for (int t = 0; t < n; ++t) {
-    long double a = two_pi * (long double)t / (long double)n;
-    dd c = host_dd(cosl(a)), s = host_dd(-sinl(a));
-    h[t] = make_float4(c.h, c.l, s.h, s.l);
-  }
-  cudaError_t e = cudaMalloc((void**)tw, sizeof(float4) * n);
+  const bool split = S > 1;
+  const int ntab = split ? n + nline : n;
+  std::vector<float4> h(ntab);
+  twiddles(n, n, h.data());
+  if (split) twiddles(nline, nline, h.data() + n);
+  cudaError_t e = cudaMalloc((void**)tw, sizeof(float4) * ntab);
   if (e != cudaSuccess) return e;
-  e = cudaMemcpy(*tw, h.data(), sizeof(float4) * n, cudaMemcpyHostToDevice);
+  e = cudaMemcpy(*tw, h.data(), sizeof(float4) * ntab, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return e;
   L->tw = *tw;
+  L->tw2 = split ? *tw + n : nullptr;
   const long double pi = 3.141592653589793238462643383279L;
   L->k.c31 = host_dd(sinl(2 * pi / 3));
   L->k.c51 = host_dd(cosl(2 * pi / 5));
@@ -377,13 +442,15 @@ cudaError_t df64_fft_create(int64_t nu, int64_t nv, Df64Fft** out) {
   cudaError_t e = make_line((int)nu, &f->lu, &f->tw_u);
   if (e == cudaSuccess) e = make_line((int)nv, &f->lv, &f->tw_v);
   const int smax = (int)(2 * kMaxSide * sizeof(float4));
-#define WG_SMEM_ATTR(TM, MB, A, Y)                                                              \
-  if (e == cudaSuccess)                                                                         \
-    e = cudaFuncSetAttribute(k_fft_lines<TM, MB, A, Y>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax)
-  WG_SMEM_ATTR(448, 2, false, false); WG_SMEM_ATTR(448, 2, false, true);
-  WG_SMEM_ATTR(448, 2, true, false);  WG_SMEM_ATTR(448, 2, true, true);
-  WG_SMEM_ATTR(832, 1, false, false); WG_SMEM_ATTR(832, 1, false, true);
-  WG_SMEM_ATTR(832, 1, true, false);  WG_SMEM_ATTR(832, 1, true, true);
+#define WG_SMEM_ATTR(TM, MB, A, Y, P)                                                           \
+  if (e == cudaSuccess)                                                                          \
+    e = cudaFuncSetAttribute(k_fft_lines<TM, MB, A, Y, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax)
+  WG_SMEM_ATTR(448, 2, false, false, false); WG_SMEM_ATTR(448, 2, false, true, false);
+  WG_SMEM_ATTR(448, 2, true, false, false);  WG_SMEM_ATTR(448, 2, true, true, false);
+  WG_SMEM_ATTR(832, 1, false, false, false); WG_SMEM_ATTR(832, 1, false, true, false);
+  WG_SMEM_ATTR(832, 1, true, false, false);  WG_SMEM_ATTR(832, 1, true, true, false);
+  WG_SMEM_ATTR(448, 2, false, false, true);  WG_SMEM_ATTR(448, 2, true, false, true);
+  WG_SMEM_ATTR(832, 1, false, false, true);  WG_SMEM_ATTR(832, 1, true, false, true);
 #undef WG_SMEM_ATTR
   if (e != cudaSuccess) {
     if (f->tw_u) cudaFree(f->tw_u);
@@ -408,7 +475,8 @@ static cudaError_t launch_lines(const FftLine& L, double2* data, int64_t batch, 
                                 cudaStream_t s) {
   if (lines_per_plane == 0 || batch == 0) return cudaSuccess;
   const size_t smem = 2 * sizeof(float4) * (size_t)L.n;
-  const int64_t nlines = batch * lines_per_plane;
+  // split lines: L.split CTAs per line
+  const int64_t nlines = batch * lines_per_plane * L.split;
   // persistent CTAs: as many as fit the GPU at once (two per SM up to 448 threads, else one)
   int dev = 0, sms = 0;
   cudaError_t ea = cudaGetDevice(&dev);
@@ -417,19 +485,21 @@ static cudaError_t launch_lines(const FftLine& L, double2* data, int64_t batch, 
   // pairs in, every element loaded: persistent CTAs with asynchronous loads (inverse row pass
   // 40.8 -> 38.5 ms per bench grid call); doubles in (converted on load) or pruned loads: one
   // line per CTA (the persistent form measured 1.2 ms slower on the forward row pass)
-  const bool async = mode != 0 && 2 * (int64_t)lhalf >= L.n;
+  const bool async = mode != 0 && 2 * (int64_t)lhalf >= L.n && L.split == 1;
   const int64_t blocks =
       async ? std::min<int64_t>(nlines, (int64_t)sms * (L.threads <= 448 ? 2 : 1)) : nlines;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
   bool common = true;   // radices 8, 4, 5, 3 only
   for (int i = 0; i < L.nst; ++i)
     if (L.radix[i] == 2 || L.radix[i] == 7 || L.radix[i] == 11) common = false;
-#define WG_LINES1(TM, MB, A, Y)                                                                 \
-  k_fft_lines<TM, MB, A, Y><<<(unsigned)blocks, L.threads, smem, s>>>(                          \
+#define WG_LINES1(TM, MB, A, Y, P)                                                              \
+  k_fft_lines<TM, MB, A, Y, P><<<(unsigned)blocks, L.threads, smem, s>>>(                       \
       L, data, plane, lines_per_plane, line_stride, elem_stride, mode, fwd, split, skip, lhalf, \
       shalf, nlines)
-#define WG_LINES(TM, MB, A) \
-  if (async) WG_LINES1(TM, MB, A, true); else WG_LINES1(TM, MB, A, false)
+#define WG_LINES(TM, MB, A)                                                                     \
+  if (L.split > 1) WG_LINES1(TM, MB, A, false, true);                                           \
+  else if (async) WG_LINES1(TM, MB, A, true, false);                                            \
+  else WG_LINES1(TM, MB, A, false, false)
   if (L.threads <= 448) {
     if (common) { WG_LINES(448, 2, false); } else { WG_LINES(448, 2, true); }
   } else {

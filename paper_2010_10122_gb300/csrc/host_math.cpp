@@ -286,10 +286,16 @@ bool df64_line_plan(int64_t n, Df64LinePlan* lp) {
   return lp->threads <= 832;
 }
 
-bool df64_side_ok(int64_t n) {
+int df64_line_split(int64_t n) {
   Df64LinePlan lp;
-  return df64_line_plan(n, &lp);
+  if (n <= kDf64MaxSide) return df64_line_plan(n, &lp) ? 1 : 0;
+  if (n > kDf64MaxSplitSide) return 0;
+  for (int s : {2, 4})
+    if (n % s == 0 && n / s <= kDf64MaxSide) return df64_line_plan(n / s, &lp) ? s : 0;
+  return 0;
 }
+
+bool df64_side_ok(int64_t n) { return df64_line_split(n) != 0; }
 
 double rounding_gain(const PolyKernel& K, const std::vector<double>& psi_c, int64_t nx,
                      int64_t ny, double psx, double psy, int64_t nu, int64_t nv, int do_w,
@@ -542,7 +548,7 @@ int choose_plan(const PlanInput& in, PlanParams& out, char* err, int errlen) {
   }
   if (!found) {
     if (!size_ok && in.fft_impl == kFftDf64)
-      return fail("the double-float FFT supports grid sides up to 6400 only");
+      return fail("the double-float FFT supports grid sides up to 25600 only");
     return fail("no kernel in the table meets the requested epsilon");
   }
   out = best;

@@ -67,8 +67,10 @@ int64_t good_size(int64_t n, int64_t mult);
 // Plane FFT implementations.
 enum FftKind { kFftCufft2d = 1, kFftDf64 = 2, kFftPrunedZ2Z = 3 };
 // The double-float FFT keeps two lines of n complex df64 values in shared memory per CTA
-// (200 KB): sides up to 6400 whose prime factors are 2, 3, 5, 7 and 11.
+// (200 KB): sides up to 6400 whose prime factors are 2, 3, 5, 7 and 11 run one line per CTA;
+// sides up to 25600 that are 2 or 4 times such a side run each line on 2 or 4 CTAs.
 constexpr int64_t kDf64MaxSide = 6400;
+constexpr int64_t kDf64MaxSplitSide = 4 * kDf64MaxSide;
 // Radix plan and CTA size of one double-float line transform: radices 8 and 4 for the power
 // of two (2 only for n = 2 * odd), then 5, 3, 7, 11; n / 8 threads rounded up to a warp
 // multiple (at least 64).
@@ -77,6 +79,9 @@ struct Df64LinePlan {
   int radix[24];
 };
 bool df64_line_plan(int64_t n, Df64LinePlan* plan);
+// CTAs per line of the double-float FFT for side n: 1, or the smallest S in {2, 4} with n / S
+// a supported single-CTA side; 0 if n is not supported
+int df64_line_split(int64_t n);
 bool df64_side_ok(int64_t n);
 
 // Gain of plane rounding into the result.  A plane value perturbed by a relative (normwise)

@@ -1,6 +1,7 @@
 // C ABI of the GB300 w-gridder (include/wgrid.h): plans, degrid / grid pipelines, one-shot
 // calls and host-only helpers.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -8,6 +9,7 @@
 #include <limits>
 #include <memory>
 #include <string>
+#include <thread>
 
 #include "wgrid_internal.h"
 
@@ -27,6 +29,9 @@ static int set_error(int code, const char* fmt, ...) {
   g_last_error = buf;
   return code;
 }
+
+// for the other translation units of the library (wgrid_internal.h)
+int wg::report_error(int code, const char* msg) { return set_error(code, "%s", msg); }
 
 #define WG_CUDA(call)                                                                    \
   do {                                                                                   \
@@ -94,6 +99,32 @@ static void pool_free(void* ptr, cudaStream_t s) {
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // ---------------------------------------------------------------------------------------
+// allocation-free degrid: the per-call workspace lives in a file-scope device array
+// ---------------------------------------------------------------------------------------
+static_assert(WG_NOALLOC_SCRATCH_BYTES % 256 == 0, "scratch size must keep 256-byte alignment");
+static __device__ __align__(256) unsigned char g_noalloc_scratch[WG_NOALLOC_SCRATCH_BYTES];
+
+// Device address of g_noalloc_scratch on device `dev` (which must be current).  In host code the
+// array's name is only a host-side stand-in, so the address is looked up with
+// cudaGetSymbolAddress once per device and cached.
+static int noalloc_scratch(int dev, unsigned char** out) {
+  static std::mutex mu;
+  static std::vector<unsigned char*> addr;
+  std::lock_guard<std::mutex> lk(mu);
+  if ((int)addr.size() <= dev) addr.resize(dev + 1, nullptr);
+  if (addr[dev] == nullptr) {
+    void* a = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&a, g_noalloc_scratch);
+    if (e != cudaSuccess || a == nullptr)
+      return set_error(WG_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+    addr[dev] = static_cast<unsigned char*>(a);
+  }
+  *out = addr[dev];
+  return WG_OK;
+}
+
+
+// ---------------------------------------------------------------------------------------
 // plan
 // ---------------------------------------------------------------------------------------
 struct wg_plan {
@@ -135,7 +166,9 @@ struct wg_plan {
   size_t fft_ws = 0;
   size_t ws_bytes = 0;
   std::mutex fft_mu;
-  cudaStream_t last_stream = nullptr;
+  // device address of the library's static scratch array (wg_degrid_noalloc), looked up when
+  // the plan is made if its per-call workspace fits the array; null otherwise
+  unsigned char* noalloc_ws = nullptr;
 };
 
 static size_t cplx_bytes(int prec) { return prec ? 16 : 8; }
@@ -451,14 +484,19 @@ int wg_plan_create(const double* uvw, const double* freq, int64_t nrows, int64_t
   };
   if (B < pp.nw) B = align_batch(B);
   if (B < p->degrid_bs && B < pp.nw) p->degrid_bs = (int)B;   // tiny budgets: one sub-batch per batch
-  // FP64: the (de)gridding kernels are bound by the FP64 pipe, and Horner on every tile /
-  // sub-batch visit doubles their work, so each visibility's kernel values are evaluated once:
-  // with the plan when the table is small (they depend only on the plan's coordinates), else
-  // once per call when it fits a quarter of the workspace
+  // FP64: Horner on every tile / sub-batch visit would put the (de)gridding on the FP64 pipe
+  // (and double its work), so each visibility's kernel values are evaluated once: with the plan
+  // when the table is small (they depend only on the plan's coordinates), else once per call.
+  // With an automatic workspace the per-call table may take up to a quarter of the free memory
+  // on top of the plane budget (1e8 visibilities: 38 GB); under a caller's cap it must fit a
+  // quarter of the cap
   const size_t wts_bytes = (size_t)std::max<int64_t>(1, p->nvis) * 3 * kMaxG * 8;
   const bool wts_resident = precision == WG_F64 && p->nvis > 0 &&
                             wts_bytes <= std::min<size_t>((size_t)4 << 30, free_b / 16);
-  p->use_wts = precision == WG_F64 && !wts_resident && wts_bytes <= budget / 4;
+  p->use_wts = precision == WG_F64 && !wts_resident &&
+               wts_bytes <= (p->opt.max_workspace == 0 ? free_b / 4 : budget / 4);
+  const size_t wts_extra = (p->opt.max_workspace == 0 && p->use_wts) ? align_up(wts_bytes, 256) : 0;
+  budget += wts_extra;
   p->nslot = (g.alpha_w - 1 + p->degrid_bs - 1) / p->degrid_bs + 1;
   if (use_df64) {
     cudaError_t e = df64_fft_create(pp.nu, pp.nv, &p->dfft);
@@ -515,15 +553,25 @@ int wg_plan_create(const double* uvw, const double* freq, int64_t nrows, int64_t
   if (p->opt.max_workspace != 0 && p->ws_bytes > p->opt.max_workspace)
     return fail(set_error(WG_ERR_OOM, "one w-plane needs %zu bytes of workspace, above the cap %zu",
                           p->ws_bytes, (size_t)p->opt.max_workspace));
-  p->last_stream = s;
+  // plans that wg_degrid_noalloc can run: look up the static scratch array now, while the
+  // plan's device is current and allocation is allowed (under lazy module loading this is when
+  // the CUDA runtime allocates the array), so that the calls themselves allocate nothing
+  if (p->ws_bytes <= (size_t)WG_NOALLOC_SCRATCH_BYTES &&
+      (rc = noalloc_scratch(p->device, &p->noalloc_ws)) != WG_OK)
+    return fail(rc);
   *out = p.release();
   return WG_OK;
 }
 
 int wg_plan_destroy(wg_plan* plan) {
   if (plan == nullptr) return WG_OK;
-  cudaStreamSynchronize(plan->last_stream);
+  // calls on the plan may be in flight on any stream of its device: wait for all of them
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != plan->device) cudaSetDevice(plan->device);
+  cudaDeviceSynchronize();
   free_plan_device(plan);
+  if (cur >= 0 && cur != plan->device) cudaSetDevice(cur);
   delete plan;
   return WG_OK;
 }
@@ -686,7 +734,6 @@ static int degrid_impl(wg_plan* p, const R* dirty, const R* wgt, typename C2<R>:
     tm.mark(ST_GRID);
   } while (0);
   if (external_ws == nullptr) pool_free(ws, s);
-  p->last_stream = s;
   if (rc != WG_OK) return rc;
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));
@@ -757,7 +804,6 @@ static int grid_impl(wg_plan* p, const typename C2<R>::T* vis, const R* wgt, R* 
     }
   } while (0);
   pool_free(ws, s);
-  p->last_stream = s;
   if (rc != WG_OK) return rc;
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));
@@ -781,31 +827,6 @@ int wg_degrid(wg_plan* plan, const void* dirty, const void* wgt, void* vis, void
   return degrid_impl<float>(plan, (const float*)dirty, (const float*)wgt, (float2*)vis, s, stats);
 }
 
-// ---------------------------------------------------------------------------------------
-// allocation-free degrid: the per-call workspace lives in a file-scope device array
-// ---------------------------------------------------------------------------------------
-static_assert(WG_NOALLOC_SCRATCH_BYTES % 256 == 0, "scratch size must keep 256-byte alignment");
-static __device__ __align__(256) unsigned char g_noalloc_scratch[WG_NOALLOC_SCRATCH_BYTES];
-
-// Device address of g_noalloc_scratch on device `dev` (which must be current).  In host code the
-// array's name is only a host-side stand-in, so the address is looked up with
-// cudaGetSymbolAddress once per device and cached.
-static int noalloc_scratch(int dev, unsigned char** out) {
-  static std::mutex mu;
-  static std::vector<unsigned char*> addr;
-  std::lock_guard<std::mutex> lk(mu);
-  if ((int)addr.size() <= dev) addr.resize(dev + 1, nullptr);
-  if (addr[dev] == nullptr) {
-    void* a = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&a, g_noalloc_scratch);
-    if (e != cudaSuccess || a == nullptr)
-      return set_error(WG_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
-    addr[dev] = static_cast<unsigned char*>(a);
-  }
-  *out = addr[dev];
-  return WG_OK;
-}
-
 int wg_degrid_noalloc(wg_plan* plan, const void* dirty, const void* wgt, void* vis,
                       void* stream) {
   if (plan == nullptr || dirty == nullptr || (vis == nullptr && plan->nvis_total > 0))
@@ -819,8 +840,8 @@ int wg_degrid_noalloc(wg_plan* plan, const void* dirty, const void* wgt, void* v
   WG_CUDA(cudaGetDevice(&dev));
   if (dev != plan->device)
     return set_error(WG_ERR_ARG, "current device %d is not the plan's device %d", dev, plan->device);
-  unsigned char* ws = nullptr;
-  WG_TRY(noalloc_scratch(dev, &ws));
+  unsigned char* ws = plan->noalloc_ws;   // looked up by wg_plan_create
+  if (ws == nullptr) return set_error(WG_ERR_INTERNAL, "static scratch address missing");
   cudaStream_t s = (cudaStream_t)stream;
   if (plan->prec)
     return degrid_impl<double>(plan, (const double*)dirty, (const double*)wgt, (double2*)vis, s,
@@ -874,6 +895,26 @@ int wg_ms2dirty(const double* uvw, const double* freq, int64_t nrows, int64_t nc
 }
 
 const char* wg_last_error(void) { return g_last_error.c_str(); }
+
+int wg_wait(void* stream, double timeout_ms) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!(timeout_ms >= 0.0)) {   // negative (or NaN): unbounded
+    WG_CUDA(cudaStreamSynchronize(s));
+    return WG_OK;
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t e = cudaStreamQuery(s);
+    if (e == cudaSuccess) return WG_OK;
+    if (e != cudaErrorNotReady)
+      return set_error(WG_ERR_CUDA, "cudaStreamQuery: %s", cudaGetErrorString(e));
+    const double ms = std::chrono::duration<double, std::milli>(
+                          std::chrono::steady_clock::now() - t0).count();
+    if (ms >= timeout_ms)
+      return set_error(WG_ERR_TIMEOUT, "stream work not finished after %.1f ms", ms);
+    std::this_thread::sleep_for(std::chrono::microseconds(ms < 1.0 ? 20 : 200));
+  }
+}
 
 // ---------------------------------------------------------------------------------------
 // host-only helpers
@@ -979,7 +1020,8 @@ struct FftUtil {
 static int fft_util_make(FftUtil& u, int64_t nu, int64_t nv, int64_t batch, int precision, int impl) {
   if (impl == 2) {
     if (precision != WG_F64 || !df64_fft_supported(nu, nv))
-      return set_error(WG_ERR_ARG, "double-float FFT needs WG_F64 and sides <= 6400 with factors 2,3,5,7,11");
+      return set_error(WG_ERR_ARG, "double-float FFT needs WG_F64 and sides with factors 2, 3, 5, 7, 11 "
+                                   "up to 6400, or 2 or 4 times such a side up to 25600");
     cudaError_t e = df64_fft_create(nu, nv, &u.d);
     if (e != cudaSuccess) return set_error(WG_ERR_CUDA, "double-float FFT setup: %s", cudaGetErrorString(e));
     return WG_OK;

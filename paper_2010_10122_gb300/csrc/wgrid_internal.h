@@ -69,6 +69,9 @@ struct IndexView {
 
 struct PlanImpl;
 
+// Record `msg` as this thread's wg_last_error() message and return `code`.
+int report_error(int code, const char* msg);
+
 // ---- double-float FFT (fft_df64.cu) -----------------------------------------------------
 struct Df64Fft;
 bool df64_fft_supported(int64_t nu, int64_t nv);

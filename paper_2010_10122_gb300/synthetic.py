@@ -1,6 +1,6 @@
 """Seeded synthetic inputs standing in for the paper's measurement sets.
 
-The paper benchmarks on a MeerKAT L-band measurement set (Sec. 7) that is not available
+The paper benchmarks on a MeerKAT L-band measurement set (Sec. 6) that is not available
 here; these generators produce inputs with the same structure: an interferometer array with
 earth-rotation uvw tracks, several frequency channels, complex visibilities and sparse point-
 source images.  This module holds no arithmetic of the gridding method itself; the oracle

@@ -85,6 +85,7 @@ SIGNATURES = {
     "wg_ms2dirty": (_I, [_VP, _VP, _I64, _I64, _VP, _VP, _I64, _I64, _D, _D, _D, _I, _I, _VP,
                          _VP, _VP]),
     "wg_last_error": (ctypes.c_char_p, []),
+    "wg_wait": (_I, [_VP, _D]),
     "wg_kernel_table_size": (_I, []),
     "wg_kernel_table_row": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_D),
                                  ctypes.POINTER(_D), ctypes.POINTER(_D)]),
@@ -101,6 +102,7 @@ SIGNATURES = {
                             _I64, ctypes.POINTER(PlanInfo)]),
     "wg_fft_time": (_I, [_I64, _I, _I64, _I, _I, ctypes.POINTER(_D)]),
     "wg_fft2d": (_I, [_VP, _I64, _I64, _I64, _I, _I, _I, _VP]),
+    "wg_fma_peak": (_I, [_I, ctypes.POINTER(_D)]),
     "wg_version": (ctypes.c_char_p, []),
 }
 
@@ -252,6 +254,10 @@ class Plan:
                 or tuple(dirty.shape) != (self.npix_x, self.npix_y) \
                 or tuple(out.shape) != (self.nrows, self.nchan):
             raise ValueError("degrid_noalloc: wrong dtype or shape")
+        if wgt is not None and (wgt.dtype != _REAL[self.prec]
+                                or tuple(wgt.shape) != (self.nrows, self.nchan)):
+            raise ValueError("degrid_noalloc: wgt must be real of the plan's precision, "
+                             "shape (nrows, nchan)")
         with torch.cuda.device(dev):
             rc = lib().wg_degrid_noalloc(self._h, _ptr(dirty), _ptr(wgt), _ptr(out),
                                          _stream_handle(stream, dev))
@@ -429,6 +435,24 @@ def fft2d(planes, sign=-1, impl=1, stream=None):
     _check(lib().wg_fft2d(_ptr(planes), int(nu), int(nv), int(b), prec, int(impl), int(sign),
                           _stream_handle(stream, planes.device)))
     return planes
+
+
+def wait(stream=None, timeout_ms=-1.0) -> bool:
+    """Bounded host wait on a CUDA stream (wg_wait): True when its work has finished, False
+    if it is still running after ``timeout_ms`` (negative: wait without bound)."""
+    dev = _device(None) if stream is None else stream.device
+    rc = lib().wg_wait(_stream_handle(stream, dev), float(timeout_ms))
+    if rc == WG_ERR_TIMEOUT:
+        return False
+    _check(rc)
+    return True
+
+
+def fma_peak(precision="f32") -> float:
+    """Measured FMA throughput (flop/s, an FMA = 2) of the current device in FP32 or FP64."""
+    f = ctypes.c_double()
+    _check(lib().wg_fma_peak(_prec(precision), ctypes.byref(f)))
+    return f.value
 
 
 def version() -> str:

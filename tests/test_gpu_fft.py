@@ -43,6 +43,21 @@ def test_df64_against_numpy_small(wg):
     assert np.linalg.norm(a.cpu().numpy() - ref) / np.linalg.norm(ref) < 5e-14
 
 
+@pytest.mark.parametrize("shape", [(2, 12, 7040), (1, 16, 13824), (1, 13824, 16), (1, 6912, 40),
+                                   (1, 24, 25600)])
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_df64_split_lines_against_numpy(wg, shape, sign):
+    """Sides above 6400 run each line on 2 CTAs (7040, 6912) or 4 CTAs (13824, 25600), one
+    radix-2 / radix-4 decimation-in-frequency step folded into the loads; both passes (rows and
+    the strided columns) against numpy's FFT."""
+    rng = np.random.default_rng(sum(shape) + sign)
+    x = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    a = torch.from_numpy(x).cuda()
+    wg.wgrid.fft2d(a, sign=sign, impl=2)
+    ref = np.fft.fft2(x) if sign < 0 else np.fft.ifft2(x) * (shape[1] * shape[2])
+    assert np.linalg.norm(a.cpu().numpy() - ref) / np.linalg.norm(ref) < 5e-14
+
+
 def test_df64_rejects_unsupported(wg):
     a = torch.zeros((1, 64, 64), dtype=torch.complex64, device="cuda")
     with pytest.raises(wg.WgridError):
@@ -50,3 +65,6 @@ def test_df64_rejects_unsupported(wg):
     b = torch.zeros((1, 13 * 8, 64), dtype=torch.complex128, device="cuda")
     with pytest.raises(wg.WgridError):
         wg.wgrid.fft2d(b, impl=2)           # factor 13
+    c = torch.zeros((1, 8, 25856), dtype=torch.complex128, device="cuda")
+    with pytest.raises(wg.WgridError):
+        wg.wgrid.fft2d(c, impl=2)           # beyond 4 x 6400

@@ -1,9 +1,9 @@
 """GPU parity: libwgrid.so (through its C ABI) against the FP64 direct-sum oracle.
 
 The method approximates R0 (Eq. rime) and R0^dagger to a requested epsilon; the bar is the
-paper's accuracy measure (Sec. 6.2, eps_rms = relative L2 error against the direct sum) at or
+paper's accuracy measure (Sec. 5.2, eps_rms = relative L2 error against the direct sum) at or
 below the requested epsilon, on the same seeded inputs, plus the adjointness criterion of
-Sec. 6.1 (see adj_tol; the paper reports < 1e-7 single and < 1e-15 double).
+Sec. 5.1 (see adj_tol; the paper reports < 1e-7 single and < 1e-15 double).
 Small cases span several uv tiles with ragged visibility counts; full-size workloads are
 checked on sampled outputs the oracle computes one by one.
 """
@@ -20,7 +20,7 @@ from paper_2010_10122_gb300 import synthetic as S  # noqa: E402
 
 
 def adj_tol(prec, eps, fft_impl=3):
-    """Adjointness bound (Sec. 6.1).  Rounding of the planes is amplified by 1 / psi at the image
+    """Adjointness bound (Sec. 5.1).  Rounding of the planes is amplified by 1 / psi at the image
     edge, which grows as the planner lowers sigma for coarser epsilon: FP64 with cuFFT planes
     1e-14 for eps < 1e-11 (measured <= 6e-16), 5e-14 above; FP64 with the double-float plane
     FFT (rounding ~5e-15) 5e-13; FP32 1e-7 for eps <= 1e-4, 1e-6 at eps = 1e-3 (sigma = 1.15,
@@ -312,6 +312,28 @@ def test_wide_8k_sampled_fp32(wg, oracle_lib):
     ri = oracle_lib.grid(obs.uvw, obs.freq, d, obs.npix_x, obs.npix_y, obs.pixsize_x,
                          obs.pixsize_y, pixel_index=psel)
     assert oracle_lib.rel_l2(img.reshape(-1)[psel], ri) <= 1e-5
+
+
+def test_wide_8k_sampled_fp64(wg, oracle_lib):
+    """The 1e8-visibility workload at eps = 1e-12 in FP64 at full size (the planner's double-float
+    plane FFT on grid sides above 6400, each line on several CTAs): 48 sampled visibilities and
+    12 sampled pixels against the oracle."""
+    obs = S.wide_8k()
+    I = S.point_source_image(obs.npix_x, obs.npix_y, seed=0)
+    plan = wg.Plan(obs.uvw, obs.freq, obs.npix_x, obs.npix_y, obs.pixsize_x, obs.pixsize_y, 1e-12, "f64")
+    assert plan.info["fft_impl"] == 2 and plan.info["nu"] > 6400, plan.info
+    vis = plan.degrid(_cu(I)).cpu().numpy()
+    rng = np.random.default_rng(3)
+    vsel = rng.choice(obs.nvis, 48, replace=False)
+    rv = oracle_lib.degrid(obs.uvw, obs.freq, I, obs.pixsize_x, obs.pixsize_y, vis_index=vsel)
+    assert oracle_lib.rel_l2(vis.reshape(-1)[vsel], rv) <= 1e-12
+    del vis
+    d = S.complex_normal((obs.nrows, obs.nchan), seed=1)
+    img = plan.grid(_cu(d)).cpu().numpy()
+    psel = rng.choice(obs.npix_x * obs.npix_y, 12, replace=False)
+    ri = oracle_lib.grid(obs.uvw, obs.freq, d, obs.npix_x, obs.npix_y, obs.pixsize_x,
+                         obs.pixsize_y, pixel_index=psel)
+    assert oracle_lib.rel_l2(img.reshape(-1)[psel], ri) <= 1e-12
 
 
 @pytest.mark.parametrize("prec,eps,fft_impl", [("f32", 1e-5, 0), ("f64", 1e-12, 2), ("f64", 1e-10, 3)])

@@ -178,7 +178,7 @@ def test_rounding_gain_matches_its_definition(wg, prec, eps, impl):
 
 
 def test_rounding_gain_grows_as_sigma_shrinks(wg):
-    """1 / psi at the image edge grows as the oversampling drops (Sec. 3: the kernel's Fourier
+    """1 / psi at the image edge grows as the oversampling drops (Sec. 2: the kernel's Fourier
     transform decays towards |k| = 1 / (2 sigma))."""
     gains = [wg.plan_params(**_planner_case(wg)[0] | dict(precision="f64", epsilon=1e-6,
                                                           force_alpha=16, force_sigma=s))["rounding_gain"]
@@ -193,11 +193,29 @@ def test_planner_fft_kind_arguments(wg):
         _planner_case(wg, precision="f32", fft_impl=3)
     with pytest.raises(wg.WgridError):
         _planner_case(wg, precision="f64", epsilon=1e-9, fft_impl=4)
-    # grid sides beyond the double-float FFT's 6400
+    # grid sides beyond the double-float FFT's 25600
     with pytest.raises(wg.WgridError) as ei:
-        _planner_case(wg, precision="f64", epsilon=1e-9, fft_impl=2, npix_x=8192, npix_y=8192,
-                      pixsize_x=math.radians(4 / 3600), pixsize_y=math.radians(4 / 3600))
-    assert "6400" in str(ei.value)
+        _planner_case(wg, precision="f64", epsilon=1e-9, fft_impl=2, npix_x=24576, npix_y=24576,
+                      pixsize_x=math.radians(1 / 3600), pixsize_y=math.radians(1 / 3600))
+    assert "25600" in str(ei.value)
+
+
+def test_planner_double_float_fft_split_sides(wg):
+    """Sides above 6400 run each line on 2 or 4 CTAs: an 8192^2 image at eps = 1e-12 gets a
+    double-float plan whose grid side is 2 or 4 times a side the line kernel supports."""
+    _, p = _planner_case(wg, precision="f64", epsilon=1e-12, fft_impl=2, npix_x=8192, npix_y=8192,
+                         pixsize_x=math.radians(4 / 3600), pixsize_y=math.radians(4 / 3600))
+    assert p["fft_impl"] == 2 and 6400 < p["nu"] <= 25600 and p["err_model"] <= 1e-12
+    ok = False
+    for s in (2, 4):
+        m = p["nu"] // s
+        if p["nu"] % s or m > 6400:
+            continue
+        for f in (2, 3, 5, 7, 11):
+            while m % f == 0:
+                m //= f
+        ok = ok or m == 1
+    assert ok, p
 
 
 @pytest.mark.parametrize("bad", [dict(npix_x=31), dict(npix_x=30), dict(npix_y=33),

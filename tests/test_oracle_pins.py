@@ -8,7 +8,7 @@ factor, the frequency scaling, the real part of the adjoint) fails at least one 
     numpy.fft computes independently (library reduction);
   * the phase of a point source moves with u and w at the rates -2 pi l and +2 pi (n - 1)
     that Eq. (rime) prescribes (sign pins, measured by finite differences of the output);
-  * degrid and grid are adjoint (Sec. 6.1, Eq. adjointness) to FP64 rounding;
+  * degrid and grid are adjoint (Sec. 5.1, Eq. adjointness) to FP64 rounding;
   * the Hermitian transformation (u, v, w, d) -> (-u, -v, -w, d*) leaves Eq. (rime)
     invariant (Sec. 2, Eq. Hermitian-symmetry);
   * mask / weight / do_wstacking behave as App. B describes.
@@ -83,7 +83,7 @@ def _wide_case(rng, nrows=60, nchan=3, nx=48, ny=36, fov_deg=20.0):
 
 
 def test_adjointness(oracle_lib):
-    """Sec. 6.1 Eq. (adjointness): Re<R0 I, d> = <I, R0^dagger d>, to FP64 rounding."""
+    """Sec. 5.1 Eq. (adjointness): Re<R0 I, d> = <I, R0^dagger d>, to FP64 rounding."""
     rng = np.random.default_rng(2)
     uvw, freq, nx, ny, psx, psy = _wide_case(rng)
     I = rng.uniform(-0.5, 0.5, (nx, ny))
