@@ -88,10 +88,13 @@ typedef struct wg_options {
   double force_sigma;      /* >0: only consider this oversampling factor (tests) */
   int tile;                /* uv tile side in cells (16 or 32; 0 = automatic) */
   int grid_variant;        /* gridding accumulation: 0 = automatic (shared-memory atomics for
-                              WG_F32, plane-owner warps for WG_F64), 1 = shared-memory atomics,
-                              2 = plane-owner warps (deterministic); WG_F64 plans with the
-                              double-float FFT always use plane-owner warps (their planes are
-                              double-float pairs, written by that kernel only) */
+                              WG_F32, plane-owner warps for WG_F64), 1 = shared-memory atomics, 2 =
+                              plane-owner warps (deterministic), 3 = row-band owner warps
+                              (WG_F32, alpha <= 8, 32-cell tiles: each warp owns 4 rows of the
+                              tile in every plane; deterministic; other plans fall back to 1);
+                              WG_F64 plans with the double-float FFT always use plane-owner
+                              warps (their planes are double-float pairs, written by that
+                              kernel only) */
   int fft_impl;            /* plane FFTs: 0 = automatic (WG_F32: cuFFT C2C; WG_F64: the
                               cheaper of 2 and 3 whose predicted error fits epsilon),
                               1 = cuFFT 2-D, 2 = the library's double-float FFT (WG_F64 only,

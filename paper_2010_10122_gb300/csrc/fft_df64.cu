@@ -513,7 +513,8 @@ static cudaError_t launch_lines(const FftLine& L, double2* data, int64_t batch, 
 // In-place transform of `batch` nu x nv complex128 planes; sign -1 forward, +1 inverse.
 // df64_planes: the planes on the grid side are double-float pairs (float4 per complex value:
 // re hi, re lo, im hi, im lo) instead of doubles -- the forward transform's output and the
-// inverse transform's input; the image side stays complex128.
+// inverse transform's input; image_pairs: the image side (forward input, inverse output) is
+// pairs as well.
 // keep_rows = keep_cols = 0: the full 2-D transform.  Otherwise only the image block -- the first
 // and last keep_rows/2 rows and keep_cols/2 columns of a plane -- matters, and the column pass
 // (strided, the slower pass per line) runs over the image columns only:
@@ -524,39 +525,42 @@ static cudaError_t launch_lines(const FftLine& L, double2* data, int64_t batch, 
 //    image columns, then the column pass over those columns stores only the image rows (other
 //    cells are left undefined).
 cudaError_t df64_fft_exec(Df64Fft* f, double2* data, int64_t batch, int sign, cudaStream_t s,
-                          int64_t keep_rows, int64_t keep_cols, bool df64_planes) {
+                          int64_t keep_rows, int64_t keep_cols, bool df64_planes, bool image_pairs) {
   const int64_t plane = (int64_t)f->nu * f->nv;
   const int fwd = sign < 0 ? 1 : 0;
   const bool prune = keep_rows > 0 && keep_cols > 0;
   if (prune && ((keep_rows & 1) || (keep_cols & 1) || keep_rows > f->nu || keep_cols > f->nv))
     return cudaErrorInvalidValue;
+  // pass modes: 0 loads doubles and stores pairs, 1 loads pairs and stores doubles, 2 pairs
+  // in and out; the grid side is the forward output / inverse input, the image side the other
+  const int img_in = image_pairs ? 2 : 0, img_out = image_pairs ? 2 : 1;
+  const int uv_in = df64_planes ? 2 : 0, uv_out = df64_planes ? 2 : 1;
   cudaError_t e;
   if (!prune) {
-    // rows (length nv, contiguous): doubles (pairs: inverse of pair planes) -> df64; then
-    // columns (length nu, stride nv): df64 -> doubles (pairs: forward to pair planes)
-    e = launch_lines(f->lv, data, batch, plane, f->nu, f->nv, 1, !fwd && df64_planes ? 2 : 0, fwd,
+    // rows (length nv, contiguous), then columns (length nu, stride nv)
+    e = launch_lines(f->lv, data, batch, plane, f->nu, f->nv, 1, fwd ? img_in : uv_in, fwd,
                      f->nu, 0, f->nv, f->nv, s);
     if (e != cudaSuccess) return e;
-    return launch_lines(f->lu, data, batch, plane, f->nv, 1, f->nv, fwd && df64_planes ? 2 : 1, fwd,
+    return launch_lines(f->lu, data, batch, plane, f->nv, 1, f->nv, fwd ? uv_out : img_out, fwd,
                         f->nv, 0, f->nu, f->nu, s);
   }
   const int rh = (int)(keep_rows / 2);   // image half-extent along u (rows)
   const int ch = (int)(keep_cols / 2);   // along v (columns)
   const int ncols = 2 * ch, cskip = f->nv - ncols;   // image columns: [0, ch) and [nv - ch, nv)
   if (fwd) {
-    // image columns (length nu, stride nv), image rows loaded: doubles -> df64; then all rows
-    // (length nv), image columns loaded: df64 -> pairs (or doubles)
-    e = launch_lines(f->lu, data, batch, plane, ncols, 1, f->nv, 0, fwd, ch, cskip, rh, f->nu, s);
+    // image columns (length nu, stride nv), image rows loaded; then all rows (length nv),
+    // image columns loaded
+    e = launch_lines(f->lu, data, batch, plane, ncols, 1, f->nv, img_in, fwd, ch, cskip, rh,
+                     f->nu, s);
     if (e != cudaSuccess) return e;
-    return launch_lines(f->lv, data, batch, plane, f->nu, f->nv, 1, df64_planes ? 2 : 1, fwd, f->nu,
-                        0, ch, f->nv, s);
+    return launch_lines(f->lv, data, batch, plane, f->nu, f->nv, 1, uv_out, fwd, f->nu, 0, ch,
+                        f->nv, s);
   }
-  // inverse: all rows, image columns stored: pairs (or doubles) -> df64; then the image columns,
-  // image rows stored: df64 -> doubles
-  e = launch_lines(f->lv, data, batch, plane, f->nu, f->nv, 1, df64_planes ? 2 : 0, fwd, f->nu, 0,
-                   f->nv, ch, s);
+  // inverse: all rows, image columns stored; then the image columns, image rows stored
+  e = launch_lines(f->lv, data, batch, plane, f->nu, f->nv, 1, uv_in, fwd, f->nu, 0, f->nv, ch, s);
   if (e != cudaSuccess) return e;
-  return launch_lines(f->lu, data, batch, plane, ncols, 1, f->nv, 1, fwd, ch, cskip, f->nu, rh, s);
+  return launch_lines(f->lu, data, batch, plane, ncols, 1, f->nv, img_out, fwd, ch, cskip, f->nu,
+                      rh, s);
 }
 
 }  // namespace wg

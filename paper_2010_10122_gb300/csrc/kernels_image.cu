@@ -5,6 +5,7 @@
 // Plane layout: plane p of a batch is nu x nv complex, C order; image pixel (jx, jy) sits at
 // cell ((jx - nx/2) mod nu, (jy - ny/2) mod nv), so that a plain forward / inverse 2-D DFT
 // of the plane evaluates sum_t e^{-/+ 2 pi i (a t_x / nu + b t_y / nv)} with t = j - n/2.
+#include "df64.cuh"
 #include "wgrid_internal.h"
 
 namespace wg {
@@ -235,6 +236,115 @@ cudaError_t launch_accumulate(const Geom& g, const Z4<R>* table, const typename 
                               cudaStream_t s) {
   dim3 grid((g.ny + 255) / 256, g.nx);
   k_accumulate<R><<<grid, 256, 0, s>>>(g, table, planes, b0, nb, acc, first ? 1 : 0,
+                                       last ? 1 : 0, dirty);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// double-float image side (FP64 plans with the double-float FFT): the planes hold float pairs
+// (float4 per cell: re hi, re lo, im hi, im lo) on the image side as well, so the screen and
+// the accumulation run in pair arithmetic on the FP32 pipes instead of FP64 (GB300 issues FP64
+// FMAs at 1/64 of the FP32 rate).  The per-plane screen factor e^{2 pi i cycles(j)} is anchored
+// by an FP64 sincospi every kAnchor planes and rotated by e^{2 pi i B} in pair arithmetic in
+// between (relative error ~1e-14 per step).  Errors made here are image-domain errors: the
+// transform multiplies them by psi and the correction divides it out again, so unlike the
+// plane FFT's rounding they are not amplified by the 1 / psi correction.
+// ---------------------------------------------------------------------------------------
+struct ScreenIterDD {
+  Z4<double> t; int j, k; cdd cur, rot; double v;
+  __device__ void start(const Z4<double>& tt, int j0, double vv) {
+    t = tt; j = j0; k = 0; v = vv;
+    double rs, rc;
+    sincos2pi(t.w - rint(t.w), &rs, &rc);
+    rot.r = split_double(rc); rot.i = split_double(rs);
+    anchor();
+  }
+  __device__ void anchor() {
+    double s, c;
+    sincos2pi(screen_cycles(t, j), &s, &c);
+    cur.r = split_double(c * v); cur.i = split_double(s * v);
+  }
+  __device__ void next() {
+    ++j;
+    if (++k == kAnchor) { k = 0; anchor(); }
+    else cur = c_mul(cur, rot);
+  }
+};
+
+// planes[p] = I * corr * e^{+2 pi i c_j (n - 1 - nshift)} at the image cells as float pairs
+// (the double-float FFT treats the other cells as zeros without reading them)
+__global__ void k_screen_dd(const Geom g, const double* __restrict__ dirty,
+                            const Z4<double>* __restrict__ table, float4* __restrict__ planes,
+                            int b0, int nb) {
+  const int64_t ncell = (int64_t)g.nu * g.nv;
+  const int jy = blockIdx.x * blockDim.x + threadIdx.x;
+  const int jx = blockIdx.y;
+  if (jy >= g.ny) return;
+  const int x = jx < g.nx / 2 ? g.nu - g.nx / 2 + jx : jx - g.nx / 2;
+  const int y = jy < g.ny / 2 ? g.nv - g.ny / 2 + jy : jy - g.ny / 2;
+  const int64_t cell = (int64_t)x * g.nv + y;
+  const int64_t pix = (int64_t)jx * g.ny + jy;
+  const Z4<double> t = table[pix];
+  const double val = dirty[pix] * t.u;   // I~ = I / (n Psi), Eq. R1
+  if (!g.do_w) {
+    const dd a = split_double(val);
+    planes[cell] = make_float4(a.h, a.l, 0.f, 0.f);
+    return;
+  }
+  ScreenIterDD it;
+  it.start(t, b0, val);
+  for (int p = 0; p < nb; ++p) {
+    planes[p * ncell + cell] = store_cdd(it.cur);
+    it.next();
+  }
+}
+
+cudaError_t launch_screen_dd(const Geom& g, const double* dirty, const Z4<double>* table,
+                             float4* planes, int b0, int nb, cudaStream_t s) {
+  dim3 grid((g.ny + 255) / 256, g.nx);
+  k_screen_dd<<<grid, 256, 0, s>>>(g, dirty, table, planes, b0, nb);
+  return cudaGetLastError();
+}
+
+// acc += sum_p Re(conj(screen_p) H_p) over the batch in pair arithmetic (Eq. Rad1), the
+// batch's sum added to the FP64 accumulator; on the last batch dirty = acc * corr
+__global__ void k_accumulate_dd(const Geom g, const Z4<double>* __restrict__ table,
+                                const float4* __restrict__ planes, int b0, int nb,
+                                double* __restrict__ acc, int first, int last,
+                                double* __restrict__ dirty) {
+  const int jy = blockIdx.x * blockDim.x + threadIdx.x;
+  const int jx = blockIdx.y;
+  if (jy >= g.ny) return;
+  const int x = jx < g.nx / 2 ? g.nu - g.nx / 2 + jx : jx - g.nx / 2;
+  const int y = jy < g.ny / 2 ? g.nv - g.ny / 2 + jy : jy - g.ny / 2;
+  const int64_t ncell = (int64_t)g.nu * g.nv;
+  const int64_t cell = (int64_t)x * g.nv + y;
+  const int64_t pix = (int64_t)jx * g.ny + jy;
+  const Z4<double> t = table[pix];
+  dd sum = dd_make(0.f, 0.f);
+  if (!g.do_w) {
+    const float4 h = planes[cell];
+    sum = dd_make(h.x, h.y);
+  } else {
+    ScreenIterDD it;
+    it.start(t, b0, 1.0);
+    for (int p = 0; p < nb; ++p) {
+      const cdd h = load_cdd(planes[p * ncell + cell]);
+      // Re(exp(-2 pi i cyc) h) = cos h.re + sin h.im
+      sum = dd_add(sum, dd_dot2(it.cur.r, h.r, it.cur.i, h.i, 1.0f));
+      it.next();
+    }
+  }
+  const double a = first ? join_double(sum) : acc[pix] + join_double(sum);
+  if (last) dirty[pix] = a * t.u;
+  else acc[pix] = a;
+}
+
+cudaError_t launch_accumulate_dd(const Geom& g, const Z4<double>* table, const float4* planes,
+                                 int b0, int nb, double* acc, bool first, bool last,
+                                 double* dirty, cudaStream_t s) {
+  dim3 grid((g.ny + 255) / 256, g.nx);
+  k_accumulate_dd<<<grid, 256, 0, s>>>(g, table, planes, b0, nb, acc, first ? 1 : 0,
                                        last ? 1 : 0, dirty);
   return cudaGetLastError();
 }

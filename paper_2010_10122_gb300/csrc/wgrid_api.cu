@@ -414,7 +414,7 @@ int wg_plan_create(const double* uvw, const double* freq, int64_t nrows, int64_t
   g.w0 = pp.w0; g.dw = pp.dw; g.nshift = pp.nshift;
   g.w0_dw = pp.w0 / pp.dw;
   g.grid_variant = p->opt.grid_variant;
-  if (g.grid_variant < 0 || g.grid_variant > 2) return set_error(WG_ERR_ARG, "grid_variant must be 0, 1 or 2");
+  if (g.grid_variant < 0 || g.grid_variant > 3) return set_error(WG_ERR_ARG, "grid_variant must be 0, 1, 2 or 3");
   fill_coefs(p.get());
 
   int rc = WG_OK;
@@ -473,7 +473,7 @@ int wg_plan_create(const double* uvw, const double* freq, int64_t nrows, int64_t
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return fail(set_error(WG_ERR_CUDA, "cudaMemGetInfo"));
   size_t budget = p->opt.max_workspace;
-  if (budget == 0) budget = std::min<size_t>(free_b / 2, (size_t)48 << 30);
+  if (budget == 0) budget = std::min<size_t>(free_b / 2, (size_t)96 << 30);
   const size_t plane_b = (size_t)pp.nu * pp.nv * cplx_bytes(precision);
   int64_t B = std::max<int64_t>(1, std::min<int64_t>(pp.nw, (int64_t)(budget / (2 * plane_b))));
   p->degrid_bs = precision ? degrid_subbatch<double>(g) : degrid_subbatch<float>(g);
@@ -641,7 +641,7 @@ static int run_fft(wg_plan* p, int64_t nb, void* data, void* work, int dir, cuda
     // the image occupies the first and last nx/2 rows and ny/2 columns of a plane: degrid's
     // input is zero elsewhere (and not written by the screen) and grid reads only that block
     cudaError_t e = df64_fft_exec(p->dfft, (double2*)data, nb, dir == CUFFT_FORWARD ? -1 : 1, s,
-                                  p->g.nx, p->g.ny, p->g.df64_planes != 0);
+                                  p->g.nx, p->g.ny, p->g.df64_planes != 0, p->g.df64_planes != 0);
     if (e != cudaSuccess) return set_error(WG_ERR_CUDA, "double-float FFT: %s", cudaGetErrorString(e));
     return WG_OK;
   }
@@ -717,8 +717,17 @@ static int degrid_impl(wg_plan* p, const R* dirty, const R* wgt, typename C2<R>:
     }
     for (int64_t b0 = 0; b0 < g.nw; b0 += p->batch) {
       int nb = (int)std::min<int64_t>(p->batch, g.nw - b0);
-      // with the double-float FFT the screen writes only the image cells (see df64_fft_exec)
-      e = launch_screen<R>(g, dirty, table, planes, (int)b0, nb, p->dfft != nullptr, s);
+      // with the double-float FFT the screen writes only the image cells (see df64_fft_exec);
+      // with double-float planes it writes them as pairs, in pair arithmetic
+      if constexpr (sizeof(R) == 8) {
+        if (g.df64_planes)
+          e = launch_screen_dd(g, (const double*)dirty, (const Z4<double>*)table, (float4*)planes,
+                               (int)b0, nb, s);
+        else
+          e = launch_screen<R>(g, dirty, table, planes, (int)b0, nb, p->dfft != nullptr, s);
+      } else {
+        e = launch_screen<R>(g, dirty, table, planes, (int)b0, nb, p->dfft != nullptr, s);
+      }
       if (e != cudaSuccess) { rc = set_error(WG_ERR_CUDA, "screen: %s", cudaGetErrorString(e)); break; }
       tm.mark(ST_SCREEN);
       if ((rc = run_fft(p, nb, planes, fftw, CUFFT_FORWARD, s)) != WG_OK) break;
@@ -796,8 +805,17 @@ static int grid_impl(wg_plan* p, const typename C2<R>::T* vis, const R* wgt, R* 
       tm.mark(ST_GRID);
       if ((rc = run_fft(p, nb, planes, fftw, CUFFT_INVERSE, s)) != WG_OK) break;
       tm.mark(ST_FFT);
-      e = launch_accumulate<R>(g, table, planes, (int)b0, nb, acc, b0 == 0,
-                               b0 + nb >= g.nw, dirty, s);
+      if constexpr (sizeof(R) == 8) {
+        if (g.df64_planes)
+          e = launch_accumulate_dd(g, (const Z4<double>*)table, (const float4*)planes, (int)b0, nb,
+                                   acc, b0 == 0, b0 + nb >= g.nw, (double*)dirty, s);
+        else
+          e = launch_accumulate<R>(g, table, planes, (int)b0, nb, acc, b0 == 0, b0 + nb >= g.nw,
+                                   dirty, s);
+      } else {
+        e = launch_accumulate<R>(g, table, planes, (int)b0, nb, acc, b0 == 0, b0 + nb >= g.nw,
+                                 dirty, s);
+      }
       if (e != cudaSuccess) { rc = set_error(WG_ERR_CUDA, "accumulate: %s", cudaGetErrorString(e)); break; }
       tm.mark(ST_ACCUM);
       ++nbatches;

@@ -38,7 +38,7 @@ struct Geom {
   double psx, psy;
   double w0, dw, nshift;
   double w0_dw;         // w0 / dw
-  int grid_variant;     // 0 automatic, 1 shared atomics, 2 plane-owner warps
+  int grid_variant;     // 0 automatic, 1 shared atomics, 2 plane-owner warps, 3 row-band owners
   int df64_planes;      // FP64 plans with the double-float FFT: the uv planes hold double-float
                         // pairs (float4 per cell) and (de)gridding runs in pair arithmetic
 };
@@ -78,7 +78,8 @@ bool df64_fft_supported(int64_t nu, int64_t nv);
 cudaError_t df64_fft_create(int64_t nu, int64_t nv, Df64Fft** out);
 void df64_fft_destroy(Df64Fft* f);
 cudaError_t df64_fft_exec(Df64Fft* f, double2* data, int64_t batch, int sign, cudaStream_t s,
-                          int64_t keep_rows = 0, int64_t keep_cols = 0, bool df64_planes = false);
+                          int64_t keep_rows = 0, int64_t keep_cols = 0, bool df64_planes = false,
+                          bool image_pairs = false);
 
 // ---- index kernels (kernels_index.cu) ------------------------------------------------
 cudaError_t launch_extent(const double* uvw, int64_t nrows, unsigned long long* ext4,
@@ -106,6 +107,14 @@ template <typename R>
 cudaError_t launch_accumulate(const Geom& g, const Z4<R>* table,
                               const typename C2<R>::T* planes, int b0, int nb, double* acc,
                               bool first, bool last, R* dirty, cudaStream_t s);
+
+// the same for FP64 plans whose planes hold double-float pairs on the image side as well
+// (float4 per cell), in pair arithmetic
+cudaError_t launch_screen_dd(const Geom& g, const double* dirty, const Z4<double>* table,
+                             float4* planes, int b0, int nb, cudaStream_t s);
+cudaError_t launch_accumulate_dd(const Geom& g, const Z4<double>* table, const float4* planes,
+                                 int b0, int nb, double* acc, bool first, bool last,
+                                 double* dirty, cudaStream_t s);
 
 // ---- (de)gridding kernels (kernels_grid.cu) ------------------------------------------
 // kernel values of every indexed visibility: wts[pos * 3 kMaxG + d kMaxG + j]

@@ -238,25 +238,31 @@ def test_host_inputs_are_accepted(wg):
     assert torch.equal(a, b)
 
 
-@pytest.mark.parametrize("prec,eps", [("f32", 1e-5), ("f64", 1e-10)])
+@pytest.mark.parametrize("prec,eps", [("f32", 1e-5), ("f64", 1e-10), ("f32", 1e-3)])
 def test_grid_variants_agree(wg, oracle_lib, small_ref, prec, eps):
-    """Shared-atomic and plane-owner gridding give the same image (to rounding) and both meet
-    epsilon; the plane-owner variant is bitwise reproducible."""
+    """Shared-atomic, plane-owner and (FP32) row-band-owner gridding give the same image (to
+    rounding) and all meet epsilon; the owner variants are bitwise reproducible."""
     I, d, rv, ri = small_ref
     rdt, cdt = _dt(prec)
     imgs = []
-    for variant in (1, 2):
+    for variant in ((1, 2, 3) if prec == "f32" else (1, 2)):
         plan = wg.Plan(SMALL.uvw, SMALL.freq, SMALL.npix_x, SMALL.npix_y, SMALL.pixsize_x,
                        SMALL.pixsize_y, eps, prec, grid_variant=variant)
         dd = _cu(d.astype(cdt))
         a = plan.grid(dd)
-        if variant == 2:
+        if variant >= 2:
             assert torch.equal(a, plan.grid(dd))
         img = a.cpu().numpy()
         assert oracle_lib.rel_l2(img, ri) <= eps
         imgs.append(img)
-    scale = np.abs(imgs[0]).max()
-    assert np.abs(imgs[0] - imgs[1]).max() <= (1e-5 if prec == "f32" else 1e-13) * scale
+    # summation order differs between the variants; the difference is plane rounding, amplified
+    # by the 1 / psi correction (the planner's rounding term), which grows at the low sigma of
+    # coarse epsilons
+    info = plan.info
+    r_term = math.sqrt(max(info["err_model"] ** 2 - (info["eps_kernel"] / 0.8) ** 2, 0.0))
+    tol = max(2e-6 if prec == "f32" else 1e-13, 10 * r_term)
+    for other in imgs[1:]:
+        assert oracle_lib.rel_l2(other, imgs[0]) <= tol
 
 
 @pytest.mark.parametrize("fft_impl,eps", [(1, 1e-12), (3, 1e-12), (2, 1e-12), (2, 1e-11), (2, 1e-9),
