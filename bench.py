@@ -55,14 +55,16 @@ def parse():
                     help="precision sweep on the workload: vis/s and sampled error per epsilon")
     ap.add_argument("--serve", action="store_true",
                     help="continuous-batching serving benchmark (p50/p99 latency, vis/s)")
-    ap.add_argument("--serve-requests", type=int, default=200)
-    ap.add_argument("--serve-obs", type=int, default=16)
-    ap.add_argument("--serve-sizes", default="512,1024,2048")
-    ap.add_argument("--serve-vis", default="1e5,5e6")
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-obs", type=int, default=32)
+    ap.add_argument("--serve-sizes", default="512,1024,2048,4096,8192")
+    ap.add_argument("--serve-vis", default="1e5,5e7")
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
-    ap.add_argument("--serve-load", type=float, default=0.9,
-                    help="Poisson arrival rate as a fraction of the one-at-a-time capacity")
+    ap.add_argument("--serve-loads", default="1.0",
+                    help="Poisson arrival rates as multiples of the one-at-a-time capacity")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="leave out the bounded serving sub-mix of the default run")
     ap.add_argument("--modes-1e8", default="f32,f64",
                     help="modes of the 1e8-visibility block (empty string: skip it)")
     ap.add_argument("--steps-1e8", type=int, default=2)
@@ -330,19 +332,23 @@ def run_sweep(args):
     return 0
 
 
-def run_serve(args):
+def serve_benchmark(n_requests, n_obs, sizes, vis_range, slots, budget_gb, loads, seed=5,
+                    workspace_cap_gb=8.0, serial_sample=200):
     """Continuous-batching serving benchmark: resident observations of mixed image sizes and
-    visibility counts, Poisson arrivals of mixed degrid / grid requests at mixed epsilons,
-    admission by stream slots and a device-memory budget.  Reports p50 / p99 latency and
-    aggregate vis/s, next to one-at-a-time execution of the same requests."""
+    visibility counts (64-antenna array, 16 channels, time steps chosen to hit the count),
+    Poisson arrivals of mixed degrid / grid requests at eps in {1e-4, 1e-5 (FP32), 1e-12
+    (FP64)}, admission by stream slots and a device-memory budget (plans, workspaces and
+    outputs), plans built off the scheduler thread.  The one-at-a-time capacity is measured on
+    up to `serial_sample` of the requests; the requests are then served at each load (arrival
+    rate as a multiple of that capacity).  Returns a dict of p50 / p99 latency and served vis/s
+    per load beside the one-at-a-time vis/s."""
     import torch
     from paper_2010_10122_gb300 import synthetic as S
     from paper_2010_10122_gb300.server import CudaExecutor, Request, Server, run_serial
-    rng = np.random.default_rng(5)
-    sizes = [int(x) for x in args.serve_sizes.split(",")]
-    vlo, vhi = (float(x) for x in args.serve_vis.split(","))
+    rng = np.random.default_rng(seed)
+    vlo, vhi = vis_range
     obs = {}
-    for i in range(args.serve_obs):
+    for i in range(n_obs):
         n = sizes[rng.integers(len(sizes))]
         nvis = int(np.exp(rng.uniform(np.log(vlo), np.log(vhi))))
         nt = max(1, nvis // (2016 * 16))
@@ -350,57 +356,96 @@ def run_serve(args):
         obs[f"obs{i}"] = S.array_observation(64, nt, 16, n, pix, seed=100 + i)
     keys = sorted(obs)
     epss = [(1e-4, "f32"), (1e-5, "f32"), (1e-12, "f64")]
+    # one device input per (observation, direction, precision), shared by the requests that use
+    # it (the mix would otherwise hold every request's input on the device at once)
+    inputs = {}
 
-    def make(nreq, seed):
-        r = np.random.default_rng(seed)
+    def data_for(k, direction, prec):
+        key = (k, direction, prec)
+        if key not in inputs:
+            o = obs[k]
+            seed_ = 1000 + keys.index(k)
+            if direction == "degrid":
+                inputs[key] = torch.from_numpy(S.point_source_image(o.npix_x, o.npix_y, seed=seed_)).to(
+                    "cuda", torch.float32 if prec == "f32" else torch.float64)
+            else:
+                inputs[key] = torch.from_numpy(S.complex_normal((o.nrows, o.nchan), seed=seed_)).to(
+                    "cuda", torch.complex64 if prec == "f32" else torch.complex128)
+        return inputs[key]
+
+    def make(nreq, s_):
+        r = np.random.default_rng(s_)
         out = []
         for _ in range(nreq):
             k = keys[r.integers(len(keys))]
-            o = obs[k]
             eps, prec = epss[r.integers(len(epss))]
-            if r.uniform() < 0.5:
-                data = torch.from_numpy(S.point_source_image(o.npix_x, o.npix_y, seed=int(r.integers(1 << 30)))).to(
-                    "cuda", torch.float32 if prec == "f32" else torch.float64)
-                out.append(Request(k, "degrid", data, eps, prec))
-            else:
-                data = torch.from_numpy(S.complex_normal((o.nrows, o.nchan), seed=int(r.integers(1 << 30)))).to(
-                    "cuda", torch.complex64 if prec == "f32" else torch.complex128)
-                out.append(Request(k, "grid", data, eps, prec))
+            direction = "degrid" if r.uniform() < 0.5 else "grid"
+            out.append(Request(k, direction, data_for(k, direction, prec), eps, prec))
         return out
 
-    budget = int(args.serve_budget_gb * (1 << 30))
-    ex = CudaExecutor(obs, slots=args.serve_slots, workspace_cap=8 << 30)
-    # resident plans for every (observation, epsilon) a request can use
-    for k in keys:
-        for eps, prec in epss:
-            ex.plan_bytes(k, eps, prec)
-    # one-at-a-time capacity on a calibration set, then the same request mix served
-    calib = make(max(8, args.serve_requests // 10), 1)
-    run_serial(ex, calib)                       # warm-up
+    budget = int(budget_gb * (1 << 30))
+    ex = CudaExecutor(obs, slots=slots, workspace_cap=int(workspace_cap_gb * (1 << 30)),
+                      keep_results=False)
+    sample = make(min(serial_sample, n_requests), 2)
+    t0 = time.perf_counter()
+    for r in sample:                    # the sample's plans (built here, not timed)
+        ex.plan_bytes(r.obs, r.epsilon, r.precision)
+    plan_s = time.perf_counter() - t0
+    plan_gb = sum(ex.resident_plans().values()) / (1 << 30)
+    run_serial(ex, sample[: min(8, len(sample))])          # warm-up
     torch.cuda.synchronize()
-    reqs_serial = make(args.serve_requests, 2)
-    t_serial = run_serial(ex, reqs_serial)
-    rate = args.serve_load * len(reqs_serial) / t_serial
-    reqs = make(args.serve_requests, 2)
-    t = 0.0
-    for r in reqs:
-        t += rng.exponential(1.0 / rate)
-        r.arrival = t
-    srv = Server(ex, slots=args.serve_slots, memory_budget=budget)
-    srv.run(reqs)
-    torch.cuda.synchronize()
-    rep = srv.report()
-    nvis_total = sum(r.nvis for r in reqs if r.error is None)
-    line = {"serve": "continuous batching", "requests": len(reqs), "observations": len(obs),
-            "image_sizes": sizes, "vis_range": [vlo, vhi], "eps_mix": [e for e, _ in epss],
-            "slots": args.serve_slots, "budget_gb": args.serve_budget_gb,
-            "arrival_rate_per_s": rate, "load": args.serve_load,
-            "p50_latency_s": rep.get("p50_s"), "p99_latency_s": rep.get("p99_s"),
-            "mean_latency_s": rep.get("mean_s"), "vis_per_s": rep.get("vis_per_s"),
-            "failed": rep.get("failed"), "max_inflight": rep.get("max_inflight"),
-            "peak_memory_gb": rep.get("peak_memory", 0) / (1 << 30),
-            "one_at_a_time_s": t_serial, "one_at_a_time_vis_per_s": nvis_total / t_serial,
-            "served_span_s": rep.get("span_s")}
+    t_serial = run_serial(ex, sample)
+    serial_vis = sum(ex.plans[(r.obs, r.epsilon, r.precision)].info["nvis"] for r in sample)
+    rate_req = len(sample) / t_serial
+    del sample
+    out = {"serve": "continuous batching", "requests": n_requests, "observations": n_obs,
+           "image_sizes": sizes, "vis_range": [vlo, vhi], "eps_mix": [e for e, _ in epss],
+           "slots": slots, "budget_gb": budget_gb, "workspace_cap_gb": workspace_cap_gb,
+           "plans_built_s": round(plan_s, 1), "plans_resident_gb": round(plan_gb, 2),
+           "one_at_a_time": {"requests": min(serial_sample, n_requests), "s": t_serial,
+                             "vis_per_s": serial_vis / t_serial, "requests_per_s": rate_req},
+           "loads": [], "inputs_gb": round(sum(t.numel() * t.element_size() for t in inputs.values()) / (1 << 30), 2),
+           "warm_up": "one unreported pass at twice the capacity grows the stream-ordered pools"}
+    for load in [None] + list(loads):
+        reqs = make(n_requests, 3)
+        t = 0.0
+        arr = np.random.default_rng(11)
+        for r in reqs:
+            t += arr.exponential(1.0 / ((load or 2.0) * rate_req))
+            r.arrival = t
+        srv = Server(ex, slots=slots, memory_budget=budget)
+        srv.adopt(ex.resident_plans())     # plans already built count against the budget
+        srv.run(reqs if load is not None else reqs[: max(slots * 4, n_requests // 10)])
+        torch.cuda.synchronize()
+        rep = srv.report()
+        if load is None:
+            continue
+        out["loads"].append({"load": load, "arrival_rate_per_s": load * rate_req,
+                             "p50_latency_s": rep.get("p50_s"), "p99_latency_s": rep.get("p99_s"),
+                             "mean_latency_s": rep.get("mean_s"), "vis_per_s": rep.get("vis_per_s"),
+                             "served_span_s": rep.get("span_s"), "failed": rep.get("failed"),
+                             "max_inflight": rep.get("max_inflight"),
+                             "plan_waits": rep.get("plan_waits"),
+                             "peak_memory_gb": rep.get("peak_memory", 0) / (1 << 30)})
+        out["inputs_gb"] = round(sum(t.numel() * t.element_size() for t in inputs.values()) / (1 << 30), 2)
+        del reqs
+        torch.cuda.empty_cache()
+    ex.close()
+    return out
+
+
+def run_serve(args):
+    """The serving benchmark at the flags' sizes (default: the full mix of 2000 requests over 32
+    observations, images 512^2 - 8192^2, 1e5 - 5e7 visibilities, 150 GB budget)."""
+    from paper_2010_10122_gb300 import _build
+    _build.build()
+    import torch
+    torch.cuda.set_device(0)
+    line = serve_benchmark(args.serve_requests, args.serve_obs,
+                           [int(x) for x in args.serve_sizes.split(",")],
+                           tuple(float(x) for x in args.serve_vis.split(",")),
+                           args.serve_slots, args.serve_budget_gb,
+                           [float(x) for x in args.serve_loads.split(",")])
     print(json.dumps(line), flush=True)
     return 0
 
@@ -800,6 +845,18 @@ def main():
     if args.modes_1e8 and ws == 1 and args.workload != "wide_8k":
         cfg8, ctx8 = run_config_1e8(args, wg, dev, hbm_peak)
 
+    # ---- serving: a bounded sub-mix of the serving workload ----------------------------------
+    serve = None
+    if ws == 1 and not args.no_serve:
+        for p in plans.values():
+            p.close()
+        plans = {}
+        torch.cuda.empty_cache()
+        serve = serve_benchmark(60, 6, [512, 1024, 2048], (1e5, 2e6), 8, 150.0, [1.0, 2.0],
+                                serial_sample=60)
+        serve["sub_mix"] = ("60 requests over 6 observations (512^2 - 2048^2, 1e5 - 2e6 "
+                            "visibilities); the full mix runs with bench.py --serve")
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         vps, cores, sample, _, vps1 = oracle_rate(obs, I, d, args.oracle_seconds)
@@ -832,7 +889,7 @@ def main():
                           "fp32_fma_tflops_measured": fp32_meas / 1e12,
                           "fp64_fma_tflops_measured": fp64_meas / 1e12},
                 "cpu_baseline": cpu, "e2e": e2e, "e2e_oneshot": e2e_one,
-                "config_1e8": cfg8,
+                "config_1e8": cfg8, "serve": serve,
                 "gpu_launches": launches * args.steps, "clocks": clk}
         print(json.dumps(line), flush=True)
     for p in plans.values():

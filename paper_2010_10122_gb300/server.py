@@ -4,10 +4,13 @@ The paper has no serving layer; this is the system pattern the build adds on top
 operator: many observations' plans (visibility index + per-pixel tables) stay resident on the
 device, requests (degrid of an image, or grid of visibilities, at a requested epsilon and
 precision) arrive over time, and each is admitted as soon as a stream slot is free and the
-device-memory budget has room for its workspace.  Admitted requests run concurrently on their
-own CUDA streams, so their kernels overlap on the GPU; completions are detected by polling
-CUDA events (bounded host waits, no device-side spin), which frees the slot and the memory for
-the next request.  Latency is measured from arrival to completion.
+device-memory budget has room for its workspace and its output.  Plans are built off the
+scheduler's thread (the executor builds them on a worker thread with its own CUDA stream):
+while a request's plan is being built the request waits and later arrivals whose plans are
+resident go ahead of it.  Admitted requests run concurrently on their own CUDA streams, so
+their kernels overlap on the GPU; completions are detected by polling CUDA events (bounded host
+waits, no device-side spin), which frees the slot and the memory for the next request.  Latency
+is measured from arrival to completion.
 
 The scheduler itself (admission, FIFO with skip-ahead, memory accounting, plan residency with
 LRU eviction, timeouts) is host logic over an executor interface, so it can be exercised on the
@@ -16,8 +19,10 @@ CPU with a fake executor; ``CudaExecutor`` runs requests through libwgrid.so.
 from __future__ import annotations
 
 import collections
+import concurrent.futures as cf
 import dataclasses
 import itertools
+import threading
 import time
 from typing import Any, Callable, Dict, List, Optional, Tuple
 
@@ -26,8 +31,8 @@ class ServerTimeout(RuntimeError):
     """A request did not complete within the server's deadline (host-side detection)."""
 
 
-@dataclasses.dataclass
-class Request:
+@dataclasses.dataclass(eq=False)   # identity: requests carry tensors, and a pending queue is
+class Request:                       # searched for the one being admitted
     obs: str                      # observation key
     direction: str                # "degrid" (image -> vis) or "grid" (vis -> image)
     data: Any                     # image (degrid) or visibilities (grid)
@@ -53,8 +58,22 @@ class Executor:
 
     def plan_bytes(self, obs: str, epsilon: float, precision: str) -> Tuple[int, int, int]:
         """(resident bytes of the plan, per-call workspace bytes, visibilities); creates the
-        plan if needed."""
+        plan if needed (blocking)."""
         raise NotImplementedError
+
+    def plan_async(self, obs: str, epsilon: float, precision: str) -> "cf.Future":
+        """A future of plan_bytes(...).  The default builds the plan right away on the calling
+        thread; executors whose plans take long to build override it with a worker thread."""
+        f: cf.Future = cf.Future()
+        try:
+            f.set_result(self.plan_bytes(obs, epsilon, precision))
+        except Exception as e:  # noqa: BLE001 - handed to the scheduler through the future
+            f.set_exception(e)
+        return f
+
+    def output_bytes(self, req: "Request") -> int:
+        """Device bytes of the request's output (charged to the memory budget while it runs)."""
+        return 0
 
     def drop_plan(self, obs: str, epsilon: float, precision: str) -> None:
         raise NotImplementedError
@@ -90,6 +109,8 @@ class Server:
         self.completed: List[Request] = []
         self.max_inflight = 0
         self.peak_memory = 0
+        self.plan_waits = 0          # admission passes that skipped a request whose plan was building
+        self._building: Dict[tuple, "cf.Future"] = {}
         self._ids = itertools.count()
 
     # ------------------------------------------------------------------ accounting
@@ -99,8 +120,19 @@ class Server:
     def memory_in_use(self) -> int:
         return sum(self.resident.values()) + self.workspace_in_use
 
-    def _ensure_plan(self, key) -> Tuple[int, int, int]:
-        resident, ws, nvis = self.ex.plan_bytes(*key)
+    def _plan_state(self, key):
+        """(resident, workspace, nvis) of a plan that is ready, None while it is being built
+        (the build is started on first use); raises the build's exception if it failed."""
+        f = self._building.get(key)
+        if f is None:
+            if key in self.resident:
+                f = self.ex.plan_async(*key)   # resident: returns at once
+            else:
+                f = self._building[key] = self.ex.plan_async(*key)
+        if not f.done():
+            return None
+        self._building.pop(key, None)
+        resident, ws, nvis = f.result()
         if key in self.resident:
             self.resident.move_to_end(key)
         else:
@@ -118,6 +150,12 @@ class Server:
             del self.resident[key]
 
     # ------------------------------------------------------------------ API
+    def adopt(self, plans: Dict[tuple, int]) -> None:
+        """Account for plans the executor already holds ({(obs, epsilon, precision): bytes}), so
+        that they count against the budget and can be evicted."""
+        for key, nbytes in plans.items():
+            self.resident[key] = nbytes
+
     def submit(self, req: Request) -> Request:
         req.rid = next(self._ids)
         if req.arrival is None or req.arrival == 0.0:
@@ -134,13 +172,18 @@ class Server:
                 break
             key = (req.obs, req.epsilon, req.precision)
             try:
-                resident, ws, nvis = self._ensure_plan(key)
+                st = self._plan_state(key)
             except Exception as e:  # plan creation failed: the request fails, others go on
                 req.error = e
                 req.done = self.now()
                 self.pending.remove(req)
                 self.completed.append(req)
                 continue
+            if st is None:          # plan still being built: later requests may go first
+                self.plan_waits += 1
+                continue
+            resident, ws, nvis = st
+            ws += self.ex.output_bytes(req)     # the output lives on the device too
             if self.memory_in_use() + ws > self.budget:
                 self._evict_for(ws, key)
             if self.memory_in_use() + ws > self.budget:
@@ -230,14 +273,17 @@ class Server:
         return {"completed": len(lat), "failed": sum(r.error is not None for r in self.completed),
                 "p50_s": q(0.5), "p99_s": q(0.99), "mean_s": sum(lat) / len(lat),
                 "span_s": span, "vis_per_s": nvis / span if span > 0 else None,
-                "max_inflight": self.max_inflight, "peak_memory": self.peak_memory}
+                "max_inflight": self.max_inflight, "peak_memory": self.peak_memory,
+                "plan_waits": self.plan_waits}
 
 
 class CudaExecutor(Executor):
-    """Runs requests through libwgrid.so, one CUDA stream per slot."""
+    """Runs requests through libwgrid.so, one CUDA stream per slot; plans are built by a worker
+    thread on a stream of its own (wg_plan_create synchronises only that stream, and ctypes
+    releases the interpreter lock during the call, so the scheduler keeps running)."""
 
     def __init__(self, observations: Dict[str, Any], slots: int, workspace_cap: int = 8 << 30,
-                 device=None):
+                 device=None, keep_results: bool = True):
         import torch
         from . import wgrid
         self.torch = torch
@@ -245,23 +291,69 @@ class CudaExecutor(Executor):
         self.obs = observations        # key -> synthetic.Observation-like (uvw, freq, npix, pixsize)
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
+        self.plan_stream = torch.cuda.Stream(device=self.device)
         self.plans: Dict[tuple, Any] = {}
         self.cap = workspace_cap
+        self._lock = threading.Lock()
+        self._builder = cf.ThreadPoolExecutor(max_workers=1, thread_name_prefix="wg-plan")
+        self._futures: Dict[tuple, "cf.Future"] = {}
+        self.keep_results = keep_results   # False: outputs are dropped once complete (benchmarks)
 
-    def plan_bytes(self, obs, epsilon, precision):
-        key = (obs, epsilon, precision)
-        p = self.plans.get(key)
-        if p is None:
-            o = self.obs[obs]
+    def _build(self, key):
+        obs, epsilon, precision = key
+        o = self.obs[obs]
+        with self.torch.cuda.device(self.device):
             p = self.wg.Plan(o.uvw, o.freq, o.npix_x, o.npix_y, o.pixsize_x, o.pixsize_y,
-                             epsilon, precision, max_workspace=self.cap, device=self.device)
+                             epsilon, precision, max_workspace=self.cap, device=self.device,
+                             stream=self.plan_stream)
+        with self._lock:
             self.plans[key] = p
         info = p.info
         return info["index_bytes"], info["workspace_bytes"], info["nvis"]
 
+    def plan_async(self, obs, epsilon, precision):
+        key = (obs, epsilon, precision)
+        with self._lock:
+            p = self.plans.get(key)
+            if p is not None:
+                f = cf.Future()
+                info = p.info
+                f.set_result((info["index_bytes"], info["workspace_bytes"], info["nvis"]))
+                return f
+            f = self._futures.get(key)
+            if f is None or (f.done() and f.exception() is not None):
+                f = self._futures[key] = self._builder.submit(self._build, key)
+            return f
+
+    def plan_bytes(self, obs, epsilon, precision):
+        return self.plan_async(obs, epsilon, precision).result()
+
+    def resident_plans(self) -> Dict[tuple, int]:
+        with self._lock:
+            return {k: p.info["index_bytes"] for k, p in self.plans.items()}
+
+    def output_bytes(self, req):
+        o = self.obs[req.obs]
+        if req.direction == "degrid":
+            return o.nrows * o.nchan * (8 if req.precision == "f32" else 16)
+        return o.npix_x * o.npix_y * (4 if req.precision == "f32" else 8)
+
     def drop_plan(self, obs, epsilon, precision):
-        p = self.plans.pop((obs, epsilon, precision), None)
+        """Forget the plan now; free it on the builder thread (wg_plan_destroy waits for the
+        device, which the scheduler thread must not do)."""
+        key = (obs, epsilon, precision)
+        with self._lock:
+            p = self.plans.pop(key, None)
+            self._futures.pop(key, None)
         if p is not None:
+            self._builder.submit(p.close)
+
+    def close(self):
+        """Wait for pending plan builds and frees, then free every plan."""
+        self._builder.shutdown(wait=True)
+        with self._lock:
+            plans, self.plans = list(self.plans.values()), {}
+        for p in plans:
             p.close()
 
     def launch(self, req, slot):
@@ -283,15 +375,17 @@ class CudaExecutor(Executor):
         return handle[0].query()
 
     def finish(self, req, handle):
-        req.result = handle[1]
+        req.result = handle[1] if self.keep_results else None
 
 
 def run_serial(executor: Executor, requests: List[Request]) -> float:
     """One-at-a-time execution of the same requests (the baseline a continuous-batching server is
-    compared with): each request is launched on slot 0 and waited for.  Returns seconds."""
-    t0 = time.perf_counter()
+    compared with): the plans are built first (not timed), then each request is launched on slot
+    0 and waited for.  Returns seconds."""
     for req in requests:
         executor.plan_bytes(req.obs, req.epsilon, req.precision)
+    t0 = time.perf_counter()
+    for req in requests:
         h = executor.launch(req, 0)
         while not executor.poll(h):
             time.sleep(1e-5)

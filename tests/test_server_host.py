@@ -1,5 +1,7 @@
 """Host logic of the continuous-batching server, with a fake executor (no GPU): admission by
 slots and memory, skip-ahead, plan residency with LRU eviction, failures and timeouts."""
+import concurrent.futures as cf
+
 import pytest
 
 from paper_2010_10122_gb300.server import Executor, Request, Server, ServerTimeout
@@ -109,6 +111,65 @@ def test_launch_failure_releases_slot():
     out = srv.run(make(2, "bad") + make(2, "a"))
     assert sum(r.error is not None for r in out) == 2 and sum(r.error is None for r in out) == 2
     assert srv.workspace_in_use == 0 and len(srv.free_slots) == 1
+
+
+class ClockFuture(cf.Future):
+    """A future that completes (with fn()) once the fake clock reaches t_ready."""
+
+    def __init__(self, clock, t_ready, fn):
+        super().__init__()
+        self.clock, self.t_ready, self.fn = clock, t_ready, fn
+
+    def done(self):
+        if not super().done() and self.clock.t >= self.t_ready:
+            self.set_result(self.fn())
+        return super().done()
+
+
+class SlowPlanExecutor(FakeExecutor):
+    """Plans of `slow` observations take `build` clock seconds to build (a future that
+    completes later, as a worker thread would); outputs take `out` bytes."""
+
+    def __init__(self, clock, sizes, duration, slow=(), build=0.2, out=0):
+        super().__init__(clock, sizes, duration)
+        self.slow, self.build, self.out = set(slow), build, out
+        self.futures = {}
+
+    def plan_async(self, obs, epsilon, precision):
+        key = (obs, epsilon, precision)
+        if obs not in self.slow or key in self.created:
+            return super().plan_async(obs, epsilon, precision)
+        if key not in self.futures:
+            self.futures[key] = ClockFuture(self.clock, self.clock.t + self.build,
+                                            lambda: self.plan_bytes(obs, epsilon, precision))
+        return self.futures[key]
+
+    def output_bytes(self, req):
+        return self.out
+
+
+def test_requests_go_ahead_of_a_plan_being_built():
+    """A request whose plan is still being built does not hold up later requests whose plans
+    are resident; it is admitted once the build finishes."""
+    clk = FakeClock()
+    ex = SlowPlanExecutor(clk, {"cold": (10, 5), "hot": (10, 5)}, {"cold": 0.01, "hot": 0.01},
+                          slow={"cold"}, build=0.3)
+    srv = Server(ex, slots=2, memory_budget=1000, clock=clk)
+    out = srv.run(make(1, "cold") + make(6, "hot", t=0.001, dt=0.01))
+    assert all(r.error is None for r in out)
+    cold = [r for r in out if r.obs == "cold"][0]
+    hot_starts = sorted(r.start for r in out if r.obs == "hot")
+    assert cold.start >= 0.3 and hot_starts[0] < 0.1 and srv.plan_waits > 0
+    assert cold.latency < 0.5          # admitted soon after its plan exists
+
+
+def test_outputs_are_charged_to_the_memory_budget():
+    clk = FakeClock()
+    ex = SlowPlanExecutor(clk, {"a": (0, 10)}, {"a": 0.05}, out=40)
+    srv = Server(ex, slots=8, memory_budget=100, clock=clk)
+    out = srv.run(make(6, "a"))
+    assert all(r.error is None for r in out)
+    assert srv.max_inflight == 2 and srv.peak_memory <= 100    # 2 x (10 + 40) fit, 3 do not
 
 
 def test_stuck_request_times_out_on_the_host():
