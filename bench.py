@@ -424,6 +424,7 @@ def serve_benchmark(n_requests, n_obs, sizes, vis_range, slots, budget_gb, loads
                              "p50_latency_s": rep.get("p50_s"), "p99_latency_s": rep.get("p99_s"),
                              "mean_latency_s": rep.get("mean_s"), "vis_per_s": rep.get("vis_per_s"),
                              "served_span_s": rep.get("span_s"), "failed": rep.get("failed"),
+                             "errors": rep.get("errors"),
                              "max_inflight": rep.get("max_inflight"),
                              "plan_waits": rep.get("plan_waits"),
                              "peak_memory_gb": rep.get("peak_memory", 0) / (1 << 30)})
@@ -584,6 +585,22 @@ def run_config_1e8(args, wg, dev, hbm_gbs):
         out["modes"][f"{prec}_eps{eps:g}"] = m
         samples[f"{prec}_eps{eps:g}"] = gpu_samples(vout, gout, vsel, psel)
         p.close()
+        # the same calls on a compact index (4 bytes per visibility and the uvw rows resident,
+        # the records recomputed per call)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pc = wg.Plan(obs.uvw, obs.freq, obs.npix_x, obs.npix_y, obs.pixsize_x, obs.pixsize_y,
+                     eps, prec, device=dev, compact_index=True)
+        cplan_ms = (time.perf_counter() - t0) * 1e3
+        pc.degrid(din, out=vout)
+        pc.grid(vin, out=gout)
+        sd = pc.degrid(din, out=vout, stats=True)[1]
+        sg = pc.grid(vin, out=gout, stats=True)[1]
+        m["compact_index"] = {"plan_ms": round(cplan_ms, 1),
+                              "index_bytes_per_vis": pc.info["index_bytes"] / max(1, obs.nvis),
+                              "degrid_ms": round(sd["ms_total"], 3), "grid_ms": round(sg["ms_total"], 3),
+                              "records_ms_per_call": round(sd["ms_prep"], 3)}
+        pc.close()
         del din, vin, vout, gout
         torch.cuda.empty_cache()
     tm = {k: mm["degrid"]["ms_total"] + mm["grid"]["ms_total"] for k, mm in out["modes"].items()}
@@ -773,10 +790,17 @@ def main():
     step_roof = {"bytes": step_bytes, "achieved_gbs": step_bytes / (ms_per_step * 1e-3) / 1e9,
                  "peak_gbs": hbm_peak, "frac": step_bytes / (hbm_peak * 1e9) / (ms_per_step * 1e-3)}
 
-    # sampled outputs of the headline workload for the error against the oracle (CPU leg)
+    # sampled outputs of the headline workload for the error against the oracle (CPU leg), and
+    # the whole outputs for the adjointness test of Sec. 5.1
     vsel2, psel2 = error_sample(obs, 256, 96, seed=0)
     samples2 = {f"{prec}_eps{eps:g}": gpu_samples(vouts[prec], gouts[prec], vsel2, psel2)
                 for prec, eps in MODES}
+    adj = {}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        from oracle import direct
+        for prec, eps in MODES:
+            adj[f"{prec}_eps{eps:g}"] = direct.adjointness_error(
+                I, vouts[prec].cpu().numpy(), d, gouts[prec].cpu().numpy())
 
     # ---- end to end: host buffers, copies inside the timed region ------------------------------
     e2e = e2e_one = None
@@ -865,6 +889,8 @@ def main():
         errs, how = oracle_errors(obs, I, d, vsel2, psel2, samples2)
         for k, e in errs.items():
             modes[k]["rel_l2_err"] = {**e, "sample": how}
+        for k, e in adj.items():
+            modes[k]["eps_adj"] = e
         if cfg8 is not None:
             o8, I8, d8, vs8, ps8, smp8 = ctx8
             errs8, how8 = oracle_errors(o8, I8, d8, vs8, ps8, smp8)

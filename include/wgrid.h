@@ -106,13 +106,22 @@ typedef struct wg_options {
                               pair arithmetic),
                               3 = pruned cuFFT Z2Z (WG_F64 only: 1-D passes that skip the
                               plane rows outside the image) */
+  int compact_index;       /* 1: the plan keeps a compact index -- 4 bytes per visibility (its
+                              position, in processing order) and a copy of uvw (24 bytes per
+                              row) -- and every call recomputes the visibilities' cell offsets,
+                              kernel coordinates and w-reference phases into its workspace
+                              (Sec. 4.3 keeps a compact index the same way), and a WG_F64 plan
+                              keeps no kernel-value table either (evaluated per call); 0
+                              (default): the plan keeps those records (32 bytes per visibility
+                              in WG_F32, 56 in WG_F64) */
 } wg_options;
 
 /* Per-call statistics (optional output).  Stage times are CUDA-event times measured on the
  * call's stream; filling them synchronises the stream at the end of the call. */
 typedef struct wg_stats {
   double ms_total;     /* whole call */
-  double ms_prep;      /* reserved (the per-pixel correction table is built with the plan) */
+  double ms_prep;      /* per-call preparation: the records of a compact index and per-call
+                          kernel values (FP64), when the plan does not keep them */
   double ms_screen;    /* w-screen + zero padding into the planes (Eq. R2) */
   double ms_fft;       /* cuFFT plane transforms (separately timed stage) */
   double ms_grid;      /* (de)gridding kernels (Eqs. R3 / Rad2) */
@@ -247,6 +256,13 @@ int wg_ms2dirty(const double* uvw, const double* freq, int64_t nrows, int64_t nc
                 const void* vis, const void* wgt, int64_t npix_x, int64_t npix_y,
                 double pixsize_x, double pixsize_y, double epsilon, int precision,
                 int do_wstacking, const uint8_t* mask, void* dirty, void* stream);
+
+/* The per-call workspaces come from a stream-ordered memory pool per device that keeps freed
+ * memory cached for the next call (no release threshold).  wg_pool_trim releases the current
+ * device's cached memory beyond keep_bytes back to the driver (cudaMemPoolTrimTo; memory of
+ * calls still in flight is not touched).  For long-running callers that mix plans of many sizes
+ * (a server), so that cached workspace does not crowd out new plans.  Errors: WG_ERR_CUDA. */
+int wg_pool_trim(size_t keep_bytes);
 
 /* Bounded host wait: returns WG_OK once all work enqueued on `stream` (void* cudaStream_t,
  * NULL = legacy default stream) so far has finished, WG_ERR_TIMEOUT if it has not finished

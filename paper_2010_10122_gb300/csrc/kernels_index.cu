@@ -220,24 +220,14 @@ cudaError_t launch_scan(uint32_t* data, int64_t n, uint32_t* scratch, cudaStream
 }
 
 // ---------------------------------------------------------------------------------------
-// Scatter: each visibility writes its record at off[key] + rank.
+// The record of visibility k at index position pos: meta (first cell inside its tile, first
+// plane), Horner coordinates of the first kernel piece, and e^{2 pi i w_k nshift}.
 // ---------------------------------------------------------------------------------------
 template <typename R>
-__global__ void k_bin_scatter(const Geom g, const double* __restrict__ uvw,
-                              const double* __restrict__ chan4,
-                              const uint32_t* __restrict__ key, const uint32_t* __restrict__ rank,
-                              const uint32_t* __restrict__ off, uint32_t* __restrict__ idx,
-                              uint32_t* __restrict__ meta, Z4<R>* __restrict__ z,
-                              typename C2<R>::T* __restrict__ ph) {
-  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= g.nvis) return;
-  uint32_t kk = key[k];
-  if (kk == kNoKey) return;
-  uint32_t pos = off[kk] + rank[k];
-  VisPos p;
-  vis_position(g, uvw, chan4, k, p);
+__device__ __forceinline__ void write_record(const Geom& g, const VisPos& p, uint32_t pos,
+                                             uint32_t* __restrict__ meta, Z4<R>* __restrict__ z,
+                                             typename C2<R>::T* __restrict__ ph) {
   int du = (int)(p.iu % g.tile), dv = (int)(p.iv % g.tile);
-  idx[pos] = (uint32_t)k | (p.fold ? kFoldBit : 0u);
   meta[pos] = (uint32_t)du | ((uint32_t)dv << 8) | ((uint32_t)p.c0 << 16);
   // Horner coordinate of the first piece: z = 2 (f + alpha/2) - 1 (Sec. 4.2)
   Z4<R> zz;
@@ -258,6 +248,28 @@ __global__ void k_bin_scatter(const Geom g, const double* __restrict__ uvw,
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Scatter: each visibility writes its index entry (k | fold bit) at off[key] + rank, and, for
+// a full index, its record (meta, z, ph may be null for a compact index).
+// ---------------------------------------------------------------------------------------
+template <typename R>
+__global__ void k_bin_scatter(const Geom g, const double* __restrict__ uvw,
+                              const double* __restrict__ chan4,
+                              const uint32_t* __restrict__ key, const uint32_t* __restrict__ rank,
+                              const uint32_t* __restrict__ off, uint32_t* __restrict__ idx,
+                              uint32_t* __restrict__ meta, Z4<R>* __restrict__ z,
+                              typename C2<R>::T* __restrict__ ph) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= g.nvis) return;
+  uint32_t kk = key[k];
+  if (kk == kNoKey) return;
+  uint32_t pos = off[kk] + rank[k];
+  VisPos p;
+  vis_position(g, uvw, chan4, k, p);
+  idx[pos] = (uint32_t)k | (p.fold ? kFoldBit : 0u);
+  if (meta != nullptr) write_record<R>(g, p, pos, meta, z, ph);
+}
+
 template <typename R>
 cudaError_t launch_bin_scatter(const Geom& g, const double* uvw, const double* chan4,
                                const uint32_t* key, const uint32_t* rank, const uint32_t* off,
@@ -270,6 +282,40 @@ cudaError_t launch_bin_scatter(const Geom& g, const double* uvw, const double* c
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------------------
+// Expansion of a compact index: the records of index positions 0 .. nvis_idx - 1 recomputed
+// from the plan's copy of uvw and the channel scales (the same FP64 arithmetic as the scatter,
+// so the records are identical to a full index's).
+// ---------------------------------------------------------------------------------------
+template <typename R>
+__global__ void k_expand(const Geom g, const double* __restrict__ uvw,
+                         const double* __restrict__ chan4, const uint32_t* __restrict__ idx,
+                         int64_t nvis_idx, uint32_t* __restrict__ meta, Z4<R>* __restrict__ z,
+                         typename C2<R>::T* __restrict__ ph) {
+  const int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (pos >= nvis_idx) return;
+  const int64_t k = idx[pos] & ~kFoldBit;
+  VisPos p;
+  vis_position(g, uvw, chan4, k, p);
+  write_record<R>(g, p, (uint32_t)pos, meta, z, ph);
+}
+
+template <typename R>
+cudaError_t launch_expand(const Geom& g, const double* uvw, const double* chan4,
+                          const uint32_t* idx, int64_t nvis_idx, uint32_t* meta, Z4<R>* z,
+                          typename C2<R>::T* ph, cudaStream_t s) {
+  if (nvis_idx == 0) return cudaSuccess;
+  k_expand<R><<<(unsigned)((nvis_idx + 255) / 256), 256, 0, s>>>(g, uvw, chan4, idx, nvis_idx,
+                                                                  meta, z, ph);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_expand<float>(const Geom&, const double*, const double*,
+                                          const uint32_t*, int64_t, uint32_t*, Z4<float>*,
+                                          float2*, cudaStream_t);
+template cudaError_t launch_expand<double>(const Geom&, const double*, const double*,
+                                           const uint32_t*, int64_t, uint32_t*, Z4<double>*,
+                                           double2*, cudaStream_t);
 template cudaError_t launch_bin_scatter<float>(const Geom&, const double*, const double*,
                                                const uint32_t*, const uint32_t*,
                                                const uint32_t*, uint32_t*, uint32_t*,

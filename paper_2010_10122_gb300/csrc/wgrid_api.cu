@@ -145,6 +145,11 @@ struct wg_plan {
   void* z = nullptr;
   void* ph = nullptr;
   void* table = nullptr;   // per pixel: 1 / (n Psi) and the w-screen phase parameters
+  // compact index: the plan keeps only idx (and a copy of uvw); every call recomputes the
+  // records (meta, z, ph) into its workspace
+  bool compact = false;
+  bool use_ph = false;      // the records carry e^{2 pi i w nshift} (w reference shifted)
+  double* uvw_dev = nullptr;
   size_t index_bytes = 0;
   Coef<float> coef_f;
   Coef<double> coef_d;
@@ -183,7 +188,7 @@ void wg_default_options(wg_options* opt) {
 
 static int free_plan_device(wg_plan* p) {
   void* ptrs[] = {p->chan4, p->cinv_u, p->cinv_v, p->off, p->idx, p->meta, p->z, p->ph, p->table,
-                  p->wts_plan};
+                  p->wts_plan, p->uvw_dev};
   for (void* q : ptrs)
     if (q != nullptr) cudaFree(q);
   if (p->has_full) cufftDestroy(p->fft_full);
@@ -254,7 +259,11 @@ static int make_fft1d(cufftHandle* h, int prec, int64_t n, int64_t stride, int64
 // per-call workspace layout
 struct Workspace {
   size_t planes = 0, fft = 0, acc = 0, wts = 0, visd = 0, total = 0;   // acc: grid accumulator / degrid partials
+  size_t rec = 0;   // compact index: the recomputed records (meta, z, ph) of every position
+  size_t rec_meta = 0, rec_z = 0;   // offsets of z and ph inside the record region
 };
+
+static size_t z_bytes(int prec) { return prec ? sizeof(Z4<double>) : sizeof(Z4<float>); }
 
 static Workspace workspace_layout(const wg_plan* p, int64_t batch, size_t fft_ws) {
   Workspace w;
@@ -266,7 +275,13 @@ static Workspace workspace_layout(const wg_plan* p, int64_t batch, size_t fft_ws
   w.wts = p->use_wts ? align_up((size_t)std::max<int64_t>(1, p->nvis) * 3 * kMaxG * 8, 256) : 0;
   // double-float planes: the gridding's prepared visibility data, a pair per part and position
   w.visd = p->g.df64_planes ? align_up((size_t)std::max<int64_t>(1, p->nvis) * 16, 256) : 0;
-  w.total = w.planes + w.fft + w.acc + w.wts + w.visd;
+  if (p->compact) {
+    const size_t n = (size_t)std::max<int64_t>(1, p->nvis);
+    w.rec_meta = align_up(n * 4, 256);
+    w.rec_z = align_up(n * z_bytes(p->prec), 256);
+    w.rec = w.rec_meta + w.rec_z + (p->use_ph ? align_up(n * cplx_bytes(p->prec), 256) : 0);
+  }
+  w.total = w.planes + w.fft + w.acc + w.wts + w.visd + w.rec;
   return w;
 }
 
@@ -302,13 +317,34 @@ static int build_index(wg_plan* p, const double* uvw, const uint8_t* mask, cudaS
     if (e != cudaSuccess) { rc = set_error(WG_ERR_CUDA, "index build: %s", cudaGetErrorString(e)); break; }
     if (herr != 0) { rc = set_error(WG_ERR_INTERNAL, "w-plane index out of range in index build"); break; }
     p->nvis = nvalid;
-    size_t zsz = p->prec ? sizeof(Z4<double>) : sizeof(Z4<float>);
+    size_t zsz = z_bytes(p->prec);
     size_t phsz = cplx_bytes(p->prec);
     size_t n = std::max<int64_t>(1, p->nvis);
+    const bool use_ph = g.do_w && g.nshift != 0.0;
+    p->use_ph = use_ph;
     if ((rc = dev_alloc(&p->idx, n)) != WG_OK) break;
+    if (p->compact) {
+      // a copy of uvw to recompute the records from; idx alone is scattered
+      const size_t nr = (size_t)std::max<int64_t>(1, p->nrows) * 3;
+      if ((rc = dev_alloc(&p->uvw_dev, nr)) != WG_OK) break;
+      if (p->nrows > 0 &&
+          (e = cudaMemcpyAsync(p->uvw_dev, uvw, sizeof(double) * 3 * p->nrows,
+                               cudaMemcpyDeviceToDevice, s)) != cudaSuccess) {
+        rc = set_error(WG_ERR_CUDA, "uvw copy: %s", cudaGetErrorString(e));
+        break;
+      }
+      if (p->prec)
+        e = launch_bin_scatter<double>(g, uvw, p->chan4, key, rank, p->off, p->idx, nullptr,
+                                       nullptr, nullptr, s);
+      else
+        e = launch_bin_scatter<float>(g, uvw, p->chan4, key, rank, p->off, p->idx, nullptr,
+                                      nullptr, nullptr, s);
+      if (e != cudaSuccess) { rc = set_error(WG_ERR_CUDA, "index scatter: %s", cudaGetErrorString(e)); break; }
+      p->index_bytes = sizeof(uint32_t) * (nkeys + 1) + n * 4 + nr * sizeof(double);
+      break;
+    }
     if ((rc = dev_alloc(&p->meta, n)) != WG_OK) break;
     if ((rc = dev_alloc((unsigned char**)&p->z, n * zsz)) != WG_OK) break;
-    bool use_ph = g.do_w && g.nshift != 0.0;
     if (use_ph && (rc = dev_alloc((unsigned char**)&p->ph, n * phsz)) != WG_OK) break;
     if (p->prec)
       e = launch_bin_scatter<double>(g, uvw, p->chan4, key, rank, p->off, p->idx, p->meta,
@@ -365,6 +401,9 @@ int wg_plan_create(const double* uvw, const double* freq, int64_t nrows, int64_t
   std::unique_ptr<wg_plan> p(new wg_plan());
   if (opt) p->opt = *opt; else wg_default_options(&p->opt);
   if (p->opt.eps_safety <= 0) p->opt.eps_safety = kDefaultEpsSafety;
+  if (p->opt.compact_index < 0 || p->opt.compact_index > 1)
+    return set_error(WG_ERR_ARG, "compact_index must be 0 or 1");
+  p->compact = p->opt.compact_index == 1;
   p->prec = precision;
   p->nrows = nrows; p->nchan = nchan; p->nvis_total = nrows * nchan;
   WG_CUDA(cudaGetDevice(&p->device));
@@ -491,7 +530,8 @@ int wg_plan_create(const double* uvw, const double* freq, int64_t nrows, int64_t
   // on top of the plane budget (1e8 visibilities: 38 GB); under a caller's cap it must fit a
   // quarter of the cap
   const size_t wts_bytes = (size_t)std::max<int64_t>(1, p->nvis) * 3 * kMaxG * 8;
-  const bool wts_resident = precision == WG_F64 && p->nvis > 0 &&
+  // (a compact plan keeps no per-visibility data beyond its index, so no resident table)
+  const bool wts_resident = precision == WG_F64 && p->nvis > 0 && !p->compact &&
                             wts_bytes <= std::min<size_t>((size_t)4 << 30, free_b / 16);
   p->use_wts = precision == WG_F64 && !wts_resident &&
                wts_bytes <= (p->opt.max_workspace == 0 ? free_b / 4 : budget / 4);
@@ -544,7 +584,20 @@ int wg_plan_create(const double* uvw, const double* freq, int64_t nrows, int64_t
     if ((rc = dev_alloc((unsigned char**)&p->wts_plan, wts_bytes)) != WG_OK) return fail(rc);
     IndexView<double> ixd{p->off, p->idx, p->meta, (const Z4<double>*)p->z,
                           (const double2*)p->ph, nullptr};
+    void* zt = nullptr;   // compact index: the Horner coordinates, recomputed for this once
+    uint32_t* mt = nullptr;
+    if (p->compact) {
+      if ((rc = pool_alloc(&zt, (size_t)p->nvis * sizeof(Z4<double>), p->device, s)) != WG_OK) return fail(rc);
+      if ((rc = pool_alloc((void**)&mt, (size_t)p->nvis * 4, p->device, s)) != WG_OK) { pool_free(zt, s); return fail(rc); }
+      cudaError_t ee = launch_expand<double>(g, p->uvw_dev, p->chan4, p->idx, p->nvis, mt,
+                                             (Z4<double>*)zt, nullptr, s);
+      if (ee != cudaSuccess) { pool_free(zt, s); pool_free(mt, s); return fail(set_error(WG_ERR_CUDA, "expand: %s", cudaGetErrorString(ee))); }
+      ixd.z = (const Z4<double>*)zt;
+      ixd.meta = mt;
+    }
     cudaError_t e = launch_weights<double>(g, p->coef_d, ixd, p->nvis, (double*)p->wts_plan, s);
+    pool_free(zt, s);
+    pool_free(mt, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(set_error(WG_ERR_CUDA, "kernel values: %s", cudaGetErrorString(e)));
     p->index_bytes += wts_bytes;
@@ -711,10 +764,20 @@ static int degrid_impl(wg_plan* p, const R* dirty, const R* wgt, typename C2<R>:
   int64_t nbatches = 0;
   do {
     cudaError_t e = cudaSuccess;
+    if (p->compact) {   // the records of the compact index, recomputed into the workspace
+      unsigned char* rb = ws + (w.total - w.rec);
+      ix.meta = (const uint32_t*)rb;
+      ix.z = (const Z4<R>*)(rb + w.rec_meta);
+      ix.ph = p->use_ph ? (const typename C2<R>::T*)(rb + w.rec_meta + w.rec_z) : nullptr;
+      e = launch_expand<R>(g, p->uvw_dev, p->chan4, p->idx, p->nvis, (uint32_t*)ix.meta,
+                           (Z4<R>*)ix.z, (typename C2<R>::T*)ix.ph, s);
+      if (e != cudaSuccess) { rc = set_error(WG_ERR_CUDA, "expand: %s", cudaGetErrorString(e)); break; }
+    }
     if (wts_call != nullptr) {
       e = launch_weights<R>(g, coef, ix, p->nvis, wts_call, s);
       if (e != cudaSuccess) { rc = set_error(WG_ERR_CUDA, "weights: %s", cudaGetErrorString(e)); break; }
     }
+    if (p->compact || wts_call != nullptr) tm.mark(ST_PREP);
     for (int64_t b0 = 0; b0 < g.nw; b0 += p->batch) {
       int nb = (int)std::min<int64_t>(p->batch, g.nw - b0);
       // with the double-float FFT the screen writes only the image cells (see df64_fft_exec);
@@ -749,7 +812,8 @@ static int degrid_impl(wg_plan* p, const R* dirty, const R* wgt, typename C2<R>:
     tm.finish(stats);
     stats->n_batches = nbatches; stats->n_planes = g.nw; stats->workspace_bytes = w.total;
     // screen + degrid per batch, finalize, weights; the double-float FFT's two passes per batch
-    stats->n_kernels = 2 * nbatches + 1 + (wts_call != nullptr) + (p->dfft != nullptr ? 2 * nbatches : 0);
+    stats->n_kernels = 2 * nbatches + 1 + (wts_call != nullptr) + (p->dfft != nullptr ? 2 * nbatches : 0) +
+                       (p->compact ? 1 : 0);
     stats->n_fft_calls = nbatches;
   }
   return WG_OK;
@@ -783,10 +847,20 @@ static int grid_impl(wg_plan* p, const typename C2<R>::T* vis, const R* wgt, R* 
   int64_t nbatches = 0;
   do {
     cudaError_t e = cudaSuccess;
+    if (p->compact) {   // the records of the compact index, recomputed into the workspace
+      unsigned char* rb = ws + (w.total - w.rec);
+      ix.meta = (const uint32_t*)rb;
+      ix.z = (const Z4<R>*)(rb + w.rec_meta);
+      ix.ph = p->use_ph ? (const typename C2<R>::T*)(rb + w.rec_meta + w.rec_z) : nullptr;
+      e = launch_expand<R>(g, p->uvw_dev, p->chan4, p->idx, p->nvis, (uint32_t*)ix.meta,
+                           (Z4<R>*)ix.z, (typename C2<R>::T*)ix.ph, s);
+      if (e != cudaSuccess) { rc = set_error(WG_ERR_CUDA, "expand: %s", cudaGetErrorString(e)); break; }
+    }
     if (wts_call != nullptr) {
       e = launch_weights<R>(g, coef, ix, p->nvis, wts_call, s);
       if (e != cudaSuccess) { rc = set_error(WG_ERR_CUDA, "weights: %s", cudaGetErrorString(e)); break; }
     }
+    if (p->compact || wts_call != nullptr) tm.mark(ST_PREP);
     // double-float planes: weights, fold and w-reference phase applied once, as pairs, and the
     // gridding kernel reads those instead of vis / wgt
     const typename C2<R>::T* vgrid = vis;
@@ -829,7 +903,7 @@ static int grid_impl(wg_plan* p, const typename C2<R>::T* vis, const R* wgt, R* 
     stats->n_batches = nbatches; stats->n_planes = g.nw; stats->workspace_bytes = w.total;
     // grid + accumulate per batch, weights; the double-float FFT's two passes per batch
     stats->n_kernels = 2 * nbatches + (wts_call != nullptr) + (p->dfft != nullptr ? 2 * nbatches : 0) +
-                       (g.df64_planes ? 1 : 0);
+                       (g.df64_planes ? 1 : 0) + (p->compact ? 1 : 0);
     stats->n_fft_calls = nbatches;
   }
   return WG_OK;
@@ -913,6 +987,15 @@ int wg_ms2dirty(const double* uvw, const double* freq, int64_t nrows, int64_t nc
 }
 
 const char* wg_last_error(void) { return g_last_error.c_str(); }
+
+int wg_pool_trim(size_t keep_bytes) {
+  int dev = 0;
+  WG_CUDA(cudaGetDevice(&dev));
+  cudaMemPool_t pool = device_pool(dev);
+  if (pool == nullptr) return set_error(WG_ERR_CUDA, "cudaMemPoolCreate failed");
+  WG_CUDA(cudaMemPoolTrimTo(pool, keep_bytes));
+  return WG_OK;
+}
 
 int wg_wait(void* stream, double timeout_ms) {
   cudaStream_t s = (cudaStream_t)stream;

@@ -95,6 +95,13 @@ cudaError_t launch_bin_scatter(const Geom& g, const double* uvw, const double* c
                                uint32_t* idx, uint32_t* meta, Z4<R>* z,
                                typename C2<R>::T* ph, cudaStream_t s);
 
+// records of a compact index (idx only) recomputed per call: meta, z and (if ph) the w-reference
+// phase of index positions 0 .. nvis_idx - 1
+template <typename R>
+cudaError_t launch_expand(const Geom& g, const double* uvw, const double* chan4,
+                          const uint32_t* idx, int64_t nvis_idx, uint32_t* meta, Z4<R>* z,
+                          typename C2<R>::T* ph, cudaStream_t s);
+
 // ---- image-side kernels (kernels_image.cu) -------------------------------------------
 // table: per pixel (corr, A, Bhi, Blo) for f32, (corr, A, B, 0) for f64; corr = 1/(n Psi).
 template <typename R>

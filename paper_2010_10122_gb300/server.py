@@ -270,7 +270,10 @@ class Server:
         q = lambda p: lat[min(len(lat) - 1, int(round(p * (len(lat) - 1))))]
         span = max(r.done for r in self.completed) - min(r.arrival for r in self.completed)
         nvis = sum(r.nvis for r in self.completed if r.error is None)
+        errors = collections.Counter(f"{type(r.error).__name__}: {str(r.error)[:80]}"
+                                     for r in self.completed if r.error is not None)
         return {"completed": len(lat), "failed": sum(r.error is not None for r in self.completed),
+                "errors": dict(errors.most_common(5)),
                 "p50_s": q(0.5), "p99_s": q(0.99), "mean_s": sum(lat) / len(lat),
                 "span_s": span, "vis_per_s": nvis / span if span > 0 else None,
                 "max_inflight": self.max_inflight, "peak_memory": self.peak_memory,
@@ -283,7 +286,7 @@ class CudaExecutor(Executor):
     releases the interpreter lock during the call, so the scheduler keeps running)."""
 
     def __init__(self, observations: Dict[str, Any], slots: int, workspace_cap: int = 8 << 30,
-                 device=None, keep_results: bool = True):
+                 device=None, keep_results: bool = True, compact: bool = True):
         import torch
         from . import wgrid
         self.torch = torch
@@ -298,14 +301,18 @@ class CudaExecutor(Executor):
         self._builder = cf.ThreadPoolExecutor(max_workers=1, thread_name_prefix="wg-plan")
         self._futures: Dict[tuple, "cf.Future"] = {}
         self.keep_results = keep_results   # False: outputs are dropped once complete (benchmarks)
+        self.compact = compact             # compact plans: index 4 B / visibility, no resident tables
 
     def _build(self, key):
         obs, epsilon, precision = key
         o = self.obs[obs]
+        # cached workspace beyond what the slots can use at once goes back to the driver first,
+        # so that it does not crowd out the plan
+        self.wg.pool_trim(len(self.streams) * self.cap, device=self.device)
         with self.torch.cuda.device(self.device):
             p = self.wg.Plan(o.uvw, o.freq, o.npix_x, o.npix_y, o.pixsize_x, o.pixsize_y,
                              epsilon, precision, max_workspace=self.cap, device=self.device,
-                             stream=self.plan_stream)
+                             stream=self.plan_stream, compact_index=self.compact)
         with self._lock:
             self.plans[key] = p
         info = p.info

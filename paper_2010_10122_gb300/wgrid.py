@@ -38,7 +38,7 @@ class Options(ctypes.Structure):
                 ("eps_safety", ctypes.c_double), ("max_workspace", ctypes.c_size_t),
                 ("force_alpha", ctypes.c_int), ("force_sigma", ctypes.c_double),
                 ("tile", ctypes.c_int), ("grid_variant", ctypes.c_int),
-                ("fft_impl", ctypes.c_int)]
+                ("fft_impl", ctypes.c_int), ("compact_index", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -86,6 +86,7 @@ SIGNATURES = {
                          _VP, _VP]),
     "wg_last_error": (ctypes.c_char_p, []),
     "wg_wait": (_I, [_VP, _D]),
+    "wg_pool_trim": (_I, [ctypes.c_size_t]),
     "wg_kernel_table_size": (_I, []),
     "wg_kernel_table_row": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_D),
                                  ctypes.POINTER(_D), ctypes.POINTER(_D)]),
@@ -190,7 +191,7 @@ class Plan:
     def __init__(self, uvw, freq, npix_x, npix_y, pixsize_x, pixsize_y, epsilon,
                  precision="f32", mask=None, do_wstacking=True, w_shift=True, eps_safety=None,
                  max_workspace=0, force_alpha=0, force_sigma=0.0, tile=0, grid_variant=0,
-                 fft_impl=0, stream=None, device=None):
+                 fft_impl=0, compact_index=False, stream=None, device=None):
         self._h = None
         dev = _device(device)
         self.device = dev
@@ -207,7 +208,7 @@ class Plan:
                               max_workspace=int(max_workspace),
                               force_alpha=int(force_alpha), force_sigma=float(force_sigma),
                               tile=int(tile), grid_variant=int(grid_variant),
-                              fft_impl=int(fft_impl))
+                              fft_impl=int(fft_impl), compact_index=int(bool(compact_index)))
         h = ctypes.c_void_p()
         with torch.cuda.device(dev):
             rc = lib().wg_plan_create(_ptr(uvw_t), _ptr(freq_t), self.nrows, self.nchan,
@@ -435,6 +436,13 @@ def fft2d(planes, sign=-1, impl=1, stream=None):
     _check(lib().wg_fft2d(_ptr(planes), int(nu), int(nv), int(b), prec, int(impl), int(sign),
                           _stream_handle(stream, planes.device)))
     return planes
+
+
+def pool_trim(keep_bytes=0, device=None) -> None:
+    """Release the library's cached per-call workspace memory on the device beyond keep_bytes."""
+    dev = _device(device)
+    with torch.cuda.device(dev):
+        _check(lib().wg_pool_trim(int(keep_bytes)))
 
 
 def wait(stream=None, timeout_ms=-1.0) -> bool:

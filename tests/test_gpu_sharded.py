@@ -1,6 +1,7 @@
 """The sharded operator's default path on the GPU: library plans on CUDA tensors with the NCCL
 collectives, in a one-rank process group (this pool gives one GPU per run; the two-rank logic
-is covered on CPU by test_sharded_gloo.py).  With one rank it must equal the plain plan."""
+is covered on CPU by test_sharded_gloo.py).  With one rank it must equal the plain plan (grid
+to rounding: summation order within a bucket differs between separately built plans)."""
 import os
 import socket
 
@@ -34,6 +35,9 @@ def test_sharded_operator_one_rank_nccl():
         d = torch.from_numpy(S.complex_normal((obs.nrows, obs.nchan), seed=2)).cuda()
         assert op.rows == (0, obs.nrows)
         assert torch.equal(op.degrid(img.clone()), plan.degrid(img))
-        assert torch.equal(op.grid(d), plan.grid(d))
+        # two separately built plans: the order inside a bucket comes from the bin-sort's
+        # atomics, so gridding agrees to rounding
+        a, b = op.grid(d), plan.grid(d)
+        assert ((a - b).norm() / b.norm()).item() <= 1e-12
     finally:
         dist.destroy_process_group()
