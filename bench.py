@@ -34,7 +34,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "visibilities/sec for degrid and grid on 1 GB300 at eps=1e-5 (FP32) and 1e-12 (FP64)"
 MODES = (("f32", 1e-5), ("f64", 1e-12))
-FFT_NAMES = {1: "cuFFT 2-D", 2: "double-float (pruned rows)", 3: "cuFFT Z2Z (pruned rows)"}
+FFT_NAMES = {1: "cuFFT 2-D", 2: "double-float (pruned rows)", 3: "cuFFT Z2Z (pruned rows)",
+             4: "library FP32 (pruned rows)"}
 
 
 def parse():
@@ -49,6 +50,8 @@ def parse():
     ap.add_argument("--oracle-seconds", type=float, default=12.0)
     ap.add_argument("--modes", default="f32,f64",
                     help="precision modes in a step (f32 = eps 1e-5, f64 = eps 1e-12)")
+    ap.add_argument("--fft-impl", type=int, default=0,
+                    help="plane FFT (0 automatic, 1 cuFFT, 4 the library's FP32 FFT for the FP32 mode)")
     ap.add_argument("--grid-variant", type=int, default=0,
                     help="gridding accumulation (0 automatic, 1 shared atomics, 2 plane-owner warps)")
     ap.add_argument("--sweep", action="store_true",
@@ -490,7 +493,7 @@ def median_stats(sts):
             ("ms_total", "ms_prep", "ms_screen", "ms_fft", "ms_grid", "ms_accum")}
 
 
-def make_plans(wg, obs, modes, dev, grid_variant=0):
+def make_plans(wg, obs, modes, dev, grid_variant=0, fft_impl=0):
     """Resident plans per precision mode, with their creation time (the index build, the
     per-pixel tables, the FFT set-up; wg_plan_create synchronises)."""
     import torch
@@ -499,7 +502,8 @@ def make_plans(wg, obs, modes, dev, grid_variant=0):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         plans[prec] = wg.Plan(obs.uvw, obs.freq, obs.npix_x, obs.npix_y, obs.pixsize_x,
-                              obs.pixsize_y, eps, prec, device=dev, grid_variant=grid_variant)
+                              obs.pixsize_y, eps, prec, device=dev, grid_variant=grid_variant,
+                              fft_impl=fft_impl if (fft_impl != 4 or prec == "f32") else 0)
         plan_ms[prec] = (time.perf_counter() - t0) * 1e3
     return plans, plan_ms
 
@@ -635,7 +639,7 @@ def main():
     obs, I, d = make_inputs(args.workload)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    plans, plan_ms = make_plans(wg, obs, MODES, dev, args.grid_variant)
+    plans, plan_ms = make_plans(wg, obs, MODES, dev, args.grid_variant, args.fft_impl)
     dins, vins, vouts, gouts = {}, {}, {}, {}
     for prec, eps in MODES:
         rdt, cdt = (torch.float32, torch.complex64) if prec == "f32" else (torch.float64, torch.complex128)

@@ -15,8 +15,8 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libwgrid.so")
-SOURCES = ["kernels_grid.cu", "kernels_image.cu", "kernels_index.cu", "fft_df64.cu", "wgrid_api.cu",
-           "peak_probe.cu", "host_math.cpp", "kernel_design.cpp"]
+SOURCES = ["kernels_grid.cu", "kernels_image.cu", "kernels_index.cu", "fft_df64.cu", "fft_f32.cu",
+           "wgrid_api.cu", "peak_probe.cu", "host_math.cpp", "kernel_design.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

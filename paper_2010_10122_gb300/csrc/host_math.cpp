@@ -297,6 +297,21 @@ int df64_line_split(int64_t n) {
 
 bool df64_side_ok(int64_t n) { return df64_line_split(n) != 0; }
 
+// The FP32 plane FFT's sides: 1, 2 or 4 CTAs per line with at most kF32SplitAbove points per
+// CTA where the side allows (else up to kF32MaxPart), each part with prime factors 2, 3, 5, 7,
+// 11 only.
+bool f32_side_ok(int64_t n) {
+  auto smooth = [](int64_t m) {
+    if (m < 2) return false;
+    for (int p : {2, 3, 5, 7, 11})
+      while (m % p == 0) m /= p;
+    return m == 1;
+  };
+  for (int s : {1, 2, 4})
+    if (n % s == 0 && n / s <= kF32MaxPart && smooth(n / s)) return true;
+  return false;
+}
+
 double rounding_gain(const PolyKernel& K, const std::vector<double>& psi_c, int64_t nx,
                      int64_t ny, double psx, double psy, int64_t nu, int64_t nv, int do_w,
                      double nshift, double dw) {
@@ -341,16 +356,17 @@ double plane_rounding(int kind, int prec, int64_t nu, int64_t nv) {
   // unit roundoff of the plane arithmetic.  c: on GB300 (2048^2 image, 1e6 visibilities,
   // alpha 16, sigma 1.5 - 2.0, gain 880 - 2.7) the double-float planes added a degrid error of
   // (4.0 - 6.1)e-15 x gain, i.e. c = 0.024 - 0.037 at 3200^2; 0.06 leaves a margin
-  double u = kind == kFftDf64 ? 0x1p-47 : (prec ? 0x1p-53 : 0x1p-24);
+  double u = kind == kFftDf64 ? 0x1p-47 : (prec ? 0x1p-53 : 0x1p-24);   // kFftF32: FP32
   const double c = 0.06;
   return c * u * std::log2((double)nu * (double)nv);
 }
 
 // Measured plane-transform times on GB300, written by calibrate_fft.py: batched cuFFT 2-D C2C
-// and Z2Z, and the library's double-float FFT (0 where it does not support the size).
+// and Z2Z, the library's double-float FFT and its FP32 FFT (0 where not measured or not
+// supported), full (unpruned) transforms.
 struct FftRow {
   int64_t n;
-  double ms32, ms64, msdf;
+  double ms32, ms64, msdf, msf32;
 };
 static const FftRow kFftTable[] = {
 #include "fft_table.inc"
@@ -359,6 +375,7 @@ static const size_t kFftRows = sizeof(kFftTable) / sizeof(kFftTable[0]);
 
 static double row_ms(const FftRow& r, int kind, int prec) {
   if (kind == kFftDf64) return r.msdf;
+  if (kind == kFftF32) return r.msf32;
   return prec ? r.ms64 : r.ms32;
 }
 
@@ -374,6 +391,9 @@ static double fft_ms_square(int64_t n, int kind, int prec) {
     double a = (double)n * n * std::log2((double)n * n), b = (double)L.n * L.n * std::log2((double)L.n * L.n);
     return ref * a / b * 1.3;   // unmeasured sizes are priced a little higher
   }
+  // the library's FP32 FFT before any calibration: priced above cuFFT's C2C (never chosen
+  // automatically, still plannable when requested)
+  if (kind == kFftF32) return 2.0 * fft_ms_square(n, kFftCufft2d, prec);
   return std::numeric_limits<double>::infinity();
 }
 
@@ -390,10 +410,17 @@ static double fft_ms(int64_t nu, int64_t nv, int kind, int prec, int64_t nx) {
   const double frac = std::min(1.0, (double)nx / (double)nu);
   if (kind == kFftPrunedZ2Z) return full * (0.5 + 0.5 * frac) * 1.07;   // 1-D plans: 7 % overhead
   if (kind == kFftDf64) return full * (0.15 + 0.85 * frac);
+  // FP32 FFT (memory-bound): the pruned passes move (1 + f)^2 / 4 of the full transform's
+  // bytes (column pass: f^2 loaded, f stored; row pass: f loaded, 1 stored; f = image fraction)
+  if (kind == kFftF32) return full * (1.0 + frac) * (1.0 + frac) / 4.0;
   return full;
 }
 
-static bool kind_supports(int kind, int64_t n) { return kind != kFftDf64 || df64_side_ok(n); }
+static bool kind_supports(int kind, int64_t n) {
+  if (kind == kFftDf64) return df64_side_ok(n);
+  if (kind == kFftF32) return f32_side_ok(n);
+  return true;
+}
 
 // Grid-size candidates >= nmin: the next measured sizes (multiples of `mult`), or FFT-friendly
 // sizes beyond the table.
@@ -451,9 +478,10 @@ int choose_plan(const PlanInput& in, PlanParams& out, char* err, int errlen) {
   if (!(in.psx > 0) || !(in.psy > 0)) return fail("pixel sizes must be positive");
   if (!(in.eps > 2e-13)) return fail("epsilon must be larger than 2e-13");
   if (in.prec == 0 && in.eps < 1e-5) return fail("single precision requires epsilon >= 1e-5");
-  if (in.fft_impl < 0 || in.fft_impl > 3) return fail("fft_impl must be 0, 1, 2 or 3");
+  if (in.fft_impl < 0 || in.fft_impl > 4) return fail("fft_impl must be 0, 1, 2, 3 or 4");
   if (in.prec == 0 && (in.fft_impl == kFftDf64 || in.fft_impl == kFftPrunedZ2Z))
     return fail("fft_impl 2 and 3 need WG_F64");
+  if (in.prec == 1 && in.fft_impl == kFftF32) return fail("fft_impl 4 needs WG_F32");
   // most negative n - 1 over the image: the corner pixel (-nx/2, -ny/2) (Sec. 2, sets L, M)
   double lmax = 0.5 * in.nx * in.psx, mmax = 0.5 * in.ny * in.psy;
   double r2 = lmax * lmax + mmax * mmax;
@@ -465,7 +493,7 @@ int choose_plan(const PlanInput& in, PlanParams& out, char* err, int errlen) {
   // double-float FFT, whichever is cheaper among those whose rounding fits epsilon
   std::vector<int> kinds;
   if (in.fft_impl != 0) kinds.push_back(in.fft_impl);
-  else if (in.prec == 0) kinds.push_back(kFftCufft2d);
+  else if (in.prec == 0) { kinds.push_back(kFftCufft2d); kinds.push_back(kFftF32); }
   else { kinds.push_back(kFftPrunedZ2Z); kinds.push_back(kFftDf64); }
 
   double safety = in.eps_safety > 0 ? in.eps_safety : kDefaultEpsSafety;
@@ -549,6 +577,8 @@ int choose_plan(const PlanInput& in, PlanParams& out, char* err, int errlen) {
   if (!found) {
     if (!size_ok && in.fft_impl == kFftDf64)
       return fail("the double-float FFT supports grid sides up to 25600 only");
+    if (!size_ok && in.fft_impl == kFftF32)
+      return fail("the FP32 plane FFT supports grid sides up to 32768 only");
     return fail("no kernel in the table meets the requested epsilon");
   }
   out = best;

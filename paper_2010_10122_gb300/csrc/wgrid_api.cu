@@ -159,6 +159,7 @@ struct wg_plan {
   cufftHandle fft_full = 0, fft_rem = 0;
   bool has_full = false, has_rem = false;
   Df64Fft* dfft = nullptr;   // double-float plane FFT (WG_F64) instead of cuFFT
+  F32Fft* ffft = nullptr;    // the library's FP32 plane FFT (WG_F32) instead of cuFFT
   // pruned cuFFT transform: 1-D row plan (rows of one image block) and column plan (all
   // columns of one plane); rows outside the image are skipped
   bool pruned = false;
@@ -196,6 +197,8 @@ static int free_plan_device(wg_plan* p) {
   p->has_full = p->has_rem = false;
   df64_fft_destroy(p->dfft);
   p->dfft = nullptr;
+  f32_fft_destroy(p->ffft);
+  p->ffft = nullptr;
   if (p->has_row) cufftDestroy(p->fft_row);
   if (p->has_col) cufftDestroy(p->fft_col);
   p->has_row = p->has_col = false;
@@ -538,7 +541,17 @@ int wg_plan_create(const double* uvw, const double* freq, int64_t nrows, int64_t
   const size_t wts_extra = (p->opt.max_workspace == 0 && p->use_wts) ? align_up(wts_bytes, 256) : 0;
   budget += wts_extra;
   p->nslot = (g.alpha_w - 1 + p->degrid_bs - 1) / p->degrid_bs + 1;
-  if (use_df64) {
+  if (pp.fft_kind == kFftF32) {
+    if (precision != WG_F32 || !f32_fft_supported(pp.nu, pp.nv))
+      return fail(set_error(WG_ERR_INTERNAL, "FP32 plane FFT does not support %lld x %lld",
+                            (long long)pp.nu, (long long)pp.nv));
+    cudaError_t e = f32_fft_create(pp.nu, pp.nv, &p->ffft);
+    if (e != cudaSuccess) return fail(set_error(WG_ERR_CUDA, "FP32 FFT setup: %s", cudaGetErrorString(e)));
+    p->fft_ws = 0;
+    while (B > 1 && workspace_layout(p.get(), B, 0).total > budget)
+      B = std::max<int64_t>(1, align_batch(B * 3 / 4));
+    p->batch = B;
+  } else if (use_df64) {
     cudaError_t e = df64_fft_create(pp.nu, pp.nv, &p->dfft);
     if (e != cudaSuccess) return fail(set_error(WG_ERR_CUDA, "double-float FFT setup: %s", cudaGetErrorString(e)));
     p->fft_ws = 0;
@@ -690,6 +703,14 @@ struct StageTimer {
 enum { ST_PREP = 0, ST_SCREEN = 1, ST_FFT = 2, ST_GRID = 3, ST_ACCUM = 4, ST_OTHER = 5 };
 
 static int run_fft(wg_plan* p, int64_t nb, void* data, void* work, int dir, cudaStream_t s) {
+  if (p->ffft != nullptr) {
+    // pruned to the image block like the double-float FFT: the screen writes only the image
+    // cells and the accumulation reads only them
+    cudaError_t e = f32_fft_exec(p->ffft, (float2*)data, nb, dir == CUFFT_FORWARD ? -1 : 1, s,
+                                 p->g.nx, p->g.ny);
+    if (e != cudaSuccess) return set_error(WG_ERR_CUDA, "FP32 FFT: %s", cudaGetErrorString(e));
+    return WG_OK;
+  }
   if (p->dfft != nullptr) {
     // the image occupies the first and last nx/2 rows and ny/2 columns of a plane: degrid's
     // input is zero elsewhere (and not written by the screen) and grid reads only that block
@@ -789,7 +810,7 @@ static int degrid_impl(wg_plan* p, const R* dirty, const R* wgt, typename C2<R>:
         else
           e = launch_screen<R>(g, dirty, table, planes, (int)b0, nb, p->dfft != nullptr, s);
       } else {
-        e = launch_screen<R>(g, dirty, table, planes, (int)b0, nb, p->dfft != nullptr, s);
+        e = launch_screen<R>(g, dirty, table, planes, (int)b0, nb, p->ffft != nullptr, s);
       }
       if (e != cudaSuccess) { rc = set_error(WG_ERR_CUDA, "screen: %s", cudaGetErrorString(e)); break; }
       tm.mark(ST_SCREEN);
@@ -812,8 +833,8 @@ static int degrid_impl(wg_plan* p, const R* dirty, const R* wgt, typename C2<R>:
     tm.finish(stats);
     stats->n_batches = nbatches; stats->n_planes = g.nw; stats->workspace_bytes = w.total;
     // screen + degrid per batch, finalize, weights; the double-float FFT's two passes per batch
-    stats->n_kernels = 2 * nbatches + 1 + (wts_call != nullptr) + (p->dfft != nullptr ? 2 * nbatches : 0) +
-                       (p->compact ? 1 : 0);
+    stats->n_kernels = 2 * nbatches + 1 + (wts_call != nullptr) +
+                       (p->dfft != nullptr || p->ffft != nullptr ? 2 * nbatches : 0) + (p->compact ? 1 : 0);
     stats->n_fft_calls = nbatches;
   }
   return WG_OK;
@@ -902,7 +923,8 @@ static int grid_impl(wg_plan* p, const typename C2<R>::T* vis, const R* wgt, R* 
     tm.finish(stats);
     stats->n_batches = nbatches; stats->n_planes = g.nw; stats->workspace_bytes = w.total;
     // grid + accumulate per batch, weights; the double-float FFT's two passes per batch
-    stats->n_kernels = 2 * nbatches + (wts_call != nullptr) + (p->dfft != nullptr ? 2 * nbatches : 0) +
+    stats->n_kernels = 2 * nbatches + (wts_call != nullptr) +
+                       (p->dfft != nullptr || p->ffft != nullptr ? 2 * nbatches : 0) +
                        (g.df64_planes ? 1 : 0) + (p->compact ? 1 : 0);
     stats->n_fft_calls = nbatches;
   }
@@ -1110,10 +1132,12 @@ struct FftUtil {
   cufftHandle h = 0;
   bool has_h = false;
   Df64Fft* d = nullptr;
+  F32Fft* f = nullptr;
   void* work = nullptr;
   ~FftUtil() {
     if (has_h) cufftDestroy(h);
     df64_fft_destroy(d);
+    f32_fft_destroy(f);
     if (work) cudaFree(work);
   }
 };
@@ -1127,7 +1151,15 @@ static int fft_util_make(FftUtil& u, int64_t nu, int64_t nv, int64_t batch, int 
     if (e != cudaSuccess) return set_error(WG_ERR_CUDA, "double-float FFT setup: %s", cudaGetErrorString(e));
     return WG_OK;
   }
-  if (impl != 1) return set_error(WG_ERR_ARG, "impl must be 1 (cuFFT) or 2 (double-float)");
+  if (impl == 4) {
+    if (precision != WG_F32 || !f32_fft_supported(nu, nv))
+      return set_error(WG_ERR_ARG, "the FP32 plane FFT needs WG_F32 and sides with factors 2, 3, 5, "
+                                   "7, 11 of at most 4096 points per CTA part (lines split in 2 or 4)");
+    cudaError_t e = f32_fft_create(nu, nv, &u.f);
+    if (e != cudaSuccess) return set_error(WG_ERR_CUDA, "FP32 FFT setup: %s", cudaGetErrorString(e));
+    return WG_OK;
+  }
+  if (impl != 1) return set_error(WG_ERR_ARG, "impl must be 1 (cuFFT), 2 (double-float) or 4 (FP32)");
   size_t ws = 0;
   WG_TRY(make_fft(&u.h, precision, nu, nv, batch, &ws));
   u.has_h = true;
@@ -1137,6 +1169,11 @@ static int fft_util_make(FftUtil& u, int64_t nu, int64_t nv, int64_t batch, int 
 }
 
 static int fft_util_exec(FftUtil& u, void* data, int64_t batch, int precision, int sign, cudaStream_t s) {
+  if (u.f != nullptr) {
+    cudaError_t e = f32_fft_exec(u.f, (float2*)data, batch, sign, s);
+    if (e != cudaSuccess) return set_error(WG_ERR_CUDA, "FP32 FFT: %s", cudaGetErrorString(e));
+    return WG_OK;
+  }
   if (u.d != nullptr) {
     cudaError_t e = df64_fft_exec(u.d, (double2*)data, batch, sign, s);
     if (e != cudaSuccess) return set_error(WG_ERR_CUDA, "double-float FFT: %s", cudaGetErrorString(e));

@@ -81,6 +81,15 @@ cudaError_t df64_fft_exec(Df64Fft* f, double2* data, int64_t batch, int sign, cu
                           int64_t keep_rows = 0, int64_t keep_cols = 0, bool df64_planes = false,
                           bool image_pairs = false);
 
+// ---- FP32 plane FFT (fft_f32.cu) -------------------------------------------------------
+struct F32Fft;
+int f32_line_split(int64_t n);   // CTAs per line for side n (0: not supported)
+bool f32_fft_supported(int64_t nu, int64_t nv);
+cudaError_t f32_fft_create(int64_t nu, int64_t nv, F32Fft** out);
+void f32_fft_destroy(F32Fft* f);
+cudaError_t f32_fft_exec(F32Fft* f, float2* data, int64_t batch, int sign, cudaStream_t s,
+                         int64_t keep_rows = 0, int64_t keep_cols = 0);
+
 // ---- index kernels (kernels_index.cu) ------------------------------------------------
 cudaError_t launch_extent(const double* uvw, int64_t nrows, unsigned long long* ext4,
                           cudaStream_t s);

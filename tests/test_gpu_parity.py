@@ -342,7 +342,19 @@ def test_wide_8k_sampled_fp64(wg, oracle_lib):
     assert oracle_lib.rel_l2(img.reshape(-1)[psel], ri) <= 1e-12
 
 
-@pytest.mark.parametrize("prec,eps,fft_impl", [("f32", 1e-5, 0), ("f64", 1e-12, 2), ("f64", 1e-10, 3)])
+@pytest.mark.parametrize("eps,w_shift", [(1e-5, 1), (1e-4, 0), (1e-3, 1)])
+def test_fp32_library_fft(wg, oracle_lib, small_ref, eps, w_shift):
+    """FP32 plans on the library's own plane FFT (fft_impl 4: pruned passes, the screen writing
+    only the image cells) against the oracle, with adjointness."""
+    I, d, rv, ri = small_ref
+    plan, vis, img = run_pair(wg, SMALL, eps, "f32", I, d, fft_impl=4, w_shift=w_shift)
+    assert plan.info["fft_impl"] == 4
+    assert oracle_lib.rel_l2(vis, rv) <= eps and oracle_lib.rel_l2(img, ri) <= eps
+    assert oracle_lib.adjointness_error(I, vis, d, img) < adj_tol("f32", eps)
+
+
+@pytest.mark.parametrize("prec,eps,fft_impl", [("f32", 1e-5, 0), ("f64", 1e-12, 2), ("f64", 1e-10, 3),
+                                               ("f32", 1e-5, 4)])
 def test_plane_batches(wg, oracle_lib, small_ref, prec, eps, fft_impl):
     """A workspace cap that holds only a few planes: the planes go through the screen / FFT /
     (de)gridding / accumulation in several batches.  Same result as one batch up to summation
