@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--no-serve", action="store_true",
                     help="leave out the bounded serving sub-mix of the default run")
     ap.add_argument("--modes-1e8", default="f32,f64",
-                    help="modes of the 1e8-visibility block (empty string: skip it)")
+                    help="modes of the 1e8-visibility block (\"none\": skip it)")
     ap.add_argument("--steps-1e8", type=int, default=2)
     ap.add_argument("--only", default=None,
                     help="profiling aid: run only one call per step, e.g. f64:grid or f32:degrid")
@@ -870,7 +870,7 @@ def main():
 
     # ---- the 1e8-visibility workload ---------------------------------------------------------
     cfg8 = ctx8 = None
-    if args.modes_1e8 and ws == 1 and args.workload != "wide_8k":
+    if args.modes_1e8 not in ("", "none") and ws == 1 and args.workload != "wide_8k":
         cfg8, ctx8 = run_config_1e8(args, wg, dev, hbm_peak)
 
     # ---- serving: a bounded sub-mix of the serving workload ----------------------------------
