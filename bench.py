@@ -342,9 +342,9 @@ def serve_benchmark(n_requests, n_obs, sizes, vis_range, slots, budget_gb, loads
     Poisson arrivals of mixed degrid / grid requests at eps in {1e-4, 1e-5 (FP32), 1e-12
     (FP64)}, admission by stream slots and a device-memory budget (plans, workspaces and
     outputs), plans built off the scheduler thread.  The one-at-a-time capacity is measured on
-    up to `serial_sample` of the requests; the requests are then served at each load (arrival
-    rate as a multiple of that capacity).  Returns a dict of p50 / p99 latency and served vis/s
-    per load beside the one-at-a-time vis/s."""
+    `serial_sample` distinct requests; the served lists repeat that mix up to `n_requests` and
+    arrive at each load (arrival rate as a multiple of that capacity).  Returns a dict of p50 /
+    p99 latency and served vis/s per load beside the one-at-a-time vis/s."""
     import torch
     from paper_2010_10122_gb300 import synthetic as S
     from paper_2010_10122_gb300.server import CudaExecutor, Request, Server, run_serial
@@ -376,20 +376,25 @@ def serve_benchmark(n_requests, n_obs, sizes, vis_range, slots, budget_gb, loads
                     "cuda", torch.complex64 if prec == "f32" else torch.complex128)
         return inputs[key]
 
+    # the request mix: `serial_sample` distinct (observation, direction, epsilon) draws; the
+    # served lists repeat that mix (each draw n_requests / serial_sample times, in a random
+    # order), so that served and one-at-a-time throughput are taken on the same composition
+    r = np.random.default_rng(2)
+    specs = []
+    for _ in range(min(serial_sample, n_requests)):
+        k = keys[r.integers(len(keys))]
+        eps, prec = epss[r.integers(len(epss))]
+        specs.append((k, "degrid" if r.uniform() < 0.5 else "grid", eps, prec))
+
     def make(nreq, s_):
-        r = np.random.default_rng(s_)
-        out = []
-        for _ in range(nreq):
-            k = keys[r.integers(len(keys))]
-            eps, prec = epss[r.integers(len(epss))]
-            direction = "degrid" if r.uniform() < 0.5 else "grid"
-            out.append(Request(k, direction, data_for(k, direction, prec), eps, prec))
-        return out
+        order = np.random.default_rng(s_).permutation(nreq) % len(specs)
+        return [Request(k, d, data_for(k, d, prec), eps, prec)
+                for k, d, eps, prec in (specs[i] for i in order)]
 
     budget = int(budget_gb * (1 << 30))
     ex = CudaExecutor(obs, slots=slots, workspace_cap=int(workspace_cap_gb * (1 << 30)),
                       keep_results=False)
-    sample = make(min(serial_sample, n_requests), 2)
+    sample = make(len(specs), 2)
     t0 = time.perf_counter()
     for r in sample:                    # the sample's plans (built here, not timed)
         ex.plan_bytes(r.obs, r.epsilon, r.precision)
@@ -405,10 +410,11 @@ def serve_benchmark(n_requests, n_obs, sizes, vis_range, slots, budget_gb, loads
            "image_sizes": sizes, "vis_range": [vlo, vhi], "eps_mix": [e for e, _ in epss],
            "slots": slots, "budget_gb": budget_gb, "workspace_cap_gb": workspace_cap_gb,
            "plans_built_s": round(plan_s, 1), "plans_resident_gb": round(plan_gb, 2),
-           "one_at_a_time": {"requests": min(serial_sample, n_requests), "s": t_serial,
+           "one_at_a_time": {"requests": len(specs), "s": t_serial,
                              "vis_per_s": serial_vis / t_serial, "requests_per_s": rate_req},
            "loads": [], "inputs_gb": round(sum(t.numel() * t.element_size() for t in inputs.values()) / (1 << 30), 2),
-           "warm_up": "one unreported pass at twice the capacity grows the stream-ordered pools"}
+           "warm_up": "one unreported pass at twice the capacity grows the stream-ordered pools",
+           "mix": f"the served lists repeat the {len(specs)} one-at-a-time requests"}
     for load in [None] + list(loads):
         reqs = make(n_requests, 3)
         t = 0.0

@@ -149,7 +149,8 @@ typedef struct wg_plan_info {
   int64_t nvis;        /* visibilities in the plan (unmasked) */
   int64_t batch;       /* w-planes per batch */
   size_t index_bytes;  /* device bytes held by the plan (visibility index, per-pixel table, and
-                          for FP64 plans of up to ~1e7 visibilities the kernel-value table) */
+                          for FP64 plans with a full index the kernel-value table, 384 bytes per
+                          visibility, when it fits a quarter of the free memory) */
   size_t workspace_bytes; /* device bytes a degrid / grid call allocates */
   double umax, vmax, wmin, wmax; /* |u|, |v| maxima and |w| range in wavelengths */
   int fft_impl;        /* plane FFT used: 1 cuFFT 2-D, 2 double-float, 3 pruned cuFFT Z2Z */

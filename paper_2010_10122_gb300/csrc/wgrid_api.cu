@@ -528,14 +528,17 @@ int wg_plan_create(const double* uvw, const double* freq, int64_t nrows, int64_t
   if (B < p->degrid_bs && B < pp.nw) p->degrid_bs = (int)B;   // tiny budgets: one sub-batch per batch
   // FP64: Horner on every tile / sub-batch visit would put the (de)gridding on the FP64 pipe
   // (and double its work), so each visibility's kernel values are evaluated once: with the plan
-  // when the table is small (they depend only on the plan's coordinates), else once per call.
+  // (they depend only on the plan's coordinates), else once per call.
   // With an automatic workspace the per-call table may take up to a quarter of the free memory
   // on top of the plane budget (1e8 visibilities: 38 GB); under a caller's cap it must fit a
   // quarter of the cap
   const size_t wts_bytes = (size_t)std::max<int64_t>(1, p->nvis) * 3 * kMaxG * 8;
-  // (a compact plan keeps no per-visibility data beyond its index, so no resident table)
+  // (a compact plan keeps no per-visibility data beyond its index, so no resident table).  A
+  // per-call table would take the same memory for the call's duration (and the workspace pool
+  // keeps it cached), so a full plan keeps the table whenever it fits a quarter of the free
+  // memory: computed once instead of on every call (1e8 visibilities: 38 GB, ~0.2 s per call)
   const bool wts_resident = precision == WG_F64 && p->nvis > 0 && !p->compact &&
-                            wts_bytes <= std::min<size_t>((size_t)4 << 30, free_b / 16);
+                            wts_bytes <= free_b / 4;
   p->use_wts = precision == WG_F64 && !wts_resident &&
                wts_bytes <= (p->opt.max_workspace == 0 ? free_b / 4 : budget / 4);
   const size_t wts_extra = (p->opt.max_workspace == 0 && p->use_wts) ? align_up(wts_bytes, 256) : 0;

@@ -309,10 +309,24 @@ class CudaExecutor(Executor):
         # cached workspace beyond what the slots can use at once goes back to the driver first,
         # so that it does not crowd out the plan
         self.wg.pool_trim(len(self.streams) * self.cap, device=self.device)
-        with self.torch.cuda.device(self.device):
-            p = self.wg.Plan(o.uvw, o.freq, o.npix_x, o.npix_y, o.pixsize_x, o.pixsize_y,
-                             epsilon, precision, max_workspace=self.cap, device=self.device,
-                             stream=self.plan_stream, compact_index=self.compact)
+        # the cap is a per-request target: an observation whose single w-plane (with its
+        # per-visibility partial sums and records) needs more gets twice the cap, up to a
+        # quarter of the device; the server admits it by the workspace the plan reports
+        cap = self.cap
+        limit = max(cap, self.torch.cuda.get_device_properties(self.device).total_memory // 4)
+        while True:
+            try:
+                with self.torch.cuda.device(self.device):
+                    p = self.wg.Plan(o.uvw, o.freq, o.npix_x, o.npix_y, o.pixsize_x,
+                                     o.pixsize_y, epsilon, precision, max_workspace=cap,
+                                     device=self.device, stream=self.plan_stream,
+                                     compact_index=self.compact)
+                break
+            except self.wg.WgridError as e:
+                if e.code != self.wg.WG_ERR_OOM or "above the cap" not in str(e) \
+                        or cap == 0 or cap >= limit:
+                    raise
+                cap = min(2 * cap, limit)
         with self._lock:
             self.plans[key] = p
         info = p.info

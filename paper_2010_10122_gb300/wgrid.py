@@ -172,6 +172,22 @@ def _stream_handle(stream, dev):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def _order(stream, dev, *tensors):
+    """A call on a caller-given stream reads tensors that were staged (or produced) on torch's
+    current stream: the given stream first waits for the current one, and the device tensors
+    are marked as used on it, so that the caching allocator does not hand their memory out
+    again before the call's kernels are done with it."""
+    if stream is None:
+        return
+    cur = torch.cuda.current_stream(dev)
+    if stream.cuda_stream == cur.cuda_stream:
+        return
+    stream.wait_stream(cur)
+    for t in tensors:
+        if t is not None and t.is_cuda:
+            t.record_stream(stream)
+
+
 def _prec(precision) -> int:
     if precision in ("f32", "float32", torch.float32, np.float32, WG_F32):
         return WG_F32
@@ -210,6 +226,7 @@ class Plan:
                               tile=int(tile), grid_variant=int(grid_variant),
                               fft_impl=int(fft_impl), compact_index=int(bool(compact_index)))
         h = ctypes.c_void_p()
+        _order(stream, dev, uvw_t, freq_t, mask_t)
         with torch.cuda.device(dev):
             rc = lib().wg_plan_create(_ptr(uvw_t), _ptr(freq_t), self.nrows, self.nchan,
                                       self.npix_x, self.npix_y, float(pixsize_x),
@@ -237,6 +254,7 @@ class Plan:
                 or not out.is_contiguous() or out.device != dev:
             raise ValueError("out: wrong dtype, shape, layout or device")
         st = Stats() if stats else None
+        _order(stream, dev, d, w, out)
         with torch.cuda.device(dev):
             rc = lib().wg_degrid(self._h, _ptr(d), _ptr(w), _ptr(out), _stream_handle(stream, dev),
                                  ctypes.byref(st) if st is not None else None)
@@ -246,7 +264,9 @@ class Plan:
     def degrid_noalloc(self, dirty, out, wgt=None, stream=None):
         """vis = R(dirty) through wg_degrid_noalloc: no allocation inside the call; ``out`` and
         the inputs must already be device tensors of the right dtype and shape, and the plan
-        must have been made with max_workspace <= NOALLOC_SCRATCH_BYTES."""
+        must have been made with max_workspace <= NOALLOC_SCRATCH_BYTES.  The call runs on
+        ``stream`` (default: the current stream) as given: the caller orders it after the work
+        that produced the inputs."""
         dev = self.device
         for t in (dirty, out) + (() if wgt is None else (wgt,)):
             if not isinstance(t, torch.Tensor) or t.device != dev or not t.is_contiguous():
@@ -276,6 +296,7 @@ class Plan:
                 or not out.is_contiguous() or out.device != dev:
             raise ValueError("out: wrong dtype, shape, layout or device")
         st = Stats() if stats else None
+        _order(stream, dev, v, w, out)
         with torch.cuda.device(dev):
             rc = lib().wg_grid(self._h, _ptr(v), _ptr(w), _ptr(out), _stream_handle(stream, dev),
                                ctypes.byref(st) if st is not None else None)
@@ -314,6 +335,7 @@ def dirty2ms(uvw, freq, dirty, wgt=None, pixsize_x=None, pixsize_y=None, epsilon
     w = _to_dev(wgt, _REAL[prec], dev, "wgt", (nrows, nchan))
     m = _to_dev(mask, torch.uint8, dev, "mask", (nrows, nchan))
     out = torch.empty((nrows, nchan), dtype=_CPLX[prec], device=dev)
+    _order(stream, dev, d, uvw_t, freq_t, w, m, out)
     with torch.cuda.device(dev):
         rc = lib().wg_dirty2ms(_ptr(uvw_t), _ptr(freq_t), nrows, nchan, _ptr(d), _ptr(w),
                                int(d.shape[0]), int(d.shape[1]), float(pixsize_x),
@@ -337,6 +359,7 @@ def ms2dirty(uvw, freq, ms, wgt=None, npix_x=None, npix_y=None, pixsize_x=None, 
     w = _to_dev(wgt, _REAL[prec], dev, "wgt", (nrows, nchan))
     m = _to_dev(mask, torch.uint8, dev, "mask", (nrows, nchan))
     out = torch.empty((int(npix_x), int(npix_y)), dtype=_REAL[prec], device=dev)
+    _order(stream, dev, v, uvw_t, freq_t, w, m, out)
     with torch.cuda.device(dev):
         rc = lib().wg_ms2dirty(_ptr(uvw_t), _ptr(freq_t), nrows, nchan, _ptr(v), _ptr(w),
                                int(npix_x), int(npix_y), float(pixsize_x), float(pixsize_y),

@@ -160,3 +160,26 @@ def test_bounded_wait_runs_out_and_recovers(wg):
     assert wg.wait(s, timeout_ms=0.0)
     x = torch.ones(4, device="cuda").sum().item()
     assert x == 4.0
+
+
+def test_calls_on_another_stream_wait_for_their_inputs():
+    """Inputs staged by the binding on torch's current stream (here: pinned host arrays copied
+    behind a busy kernel) are ready before a plan built, or an operator run, on another stream
+    reads them."""
+    import paper_2010_10122_gb300 as wg
+    obs = S.random_uvw_observation(3000, 4, 96, 80, 12.0, seed=71)
+    img = S.gaussian_image(obs.npix_x, obs.npix_y, seed=72, dtype=np.float32)
+    ref = wg.Plan(obs.uvw, obs.freq, obs.npix_x, obs.npix_y, obs.pixsize_x, obs.pixsize_y,
+                  1e-5, "f32")
+    want = ref.degrid(torch.from_numpy(img).cuda())
+    side = torch.cuda.Stream()
+    uvw = torch.from_numpy(obs.uvw).pin_memory()
+    freq = torch.from_numpy(obs.freq).pin_memory()
+    x = torch.from_numpy(img).pin_memory()
+    torch.cuda._sleep(50_000_000)            # ~25 ms of clock cycles on the current stream
+    p = wg.Plan(uvw, freq, obs.npix_x, obs.npix_y, obs.pixsize_x, obs.pixsize_y, 1e-5, "f32",
+                stream=side)
+    torch.cuda._sleep(50_000_000)
+    got = p.degrid(x, stream=side)
+    torch.cuda.synchronize()
+    assert torch.equal(got, want)

@@ -95,3 +95,20 @@ def test_memory_budget_bounds_concurrency(env):
     torch.cuda.synchronize()
     assert all(r.error is None for r in reqs)
     assert srv.peak_memory <= budget
+
+
+def test_workspace_cap_is_a_target(env):
+    """An observation whose single w-plane needs more than the executor's workspace cap gets a
+    plan with a larger workspace (the cap doubled until it fits) instead of failing."""
+    obs, CudaExecutor, Request, Server, run_serial = env
+    ex = CudaExecutor(obs, slots=1, workspace_cap=1 << 20)
+    _, ws, _ = ex.plan_bytes("a512", 1e-5, "f32")
+    assert ws > 1 << 20
+    o = obs["a512"]
+    r = Request("a512", "degrid",
+                torch.from_numpy(S.gaussian_image(o.npix_x, o.npix_y, seed=4, dtype=np.float32)).cuda(),
+                1e-5, "f32")
+    run_serial(ex, [r])
+    torch.cuda.synchronize()
+    assert r.error is None and torch.isfinite(r.result.abs()).all()
+    ex.close()
