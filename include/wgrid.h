@@ -105,7 +105,12 @@ typedef struct wg_options {
                               uv planes are then kept as double-float pairs and (de)gridded in
                               pair arithmetic),
                               3 = pruned cuFFT Z2Z (WG_F64 only: 1-D passes that skip the
-                              plane rows outside the image) */
+                              plane rows outside the image),
+                              4 = the library's FP32 FFT (WG_F32 only, never chosen
+                              automatically: pruned to the image block, but measured about 2x
+                              slower than cuFFT C2C per plane; sides up to 46340 that are 1, 2,
+                              4 or 8 times a part of at most 12800 points with prime factors 2,
+                              3, 5, 7, 11) */
   int compact_index;       /* 1: the plan keeps a compact index -- 4 bytes per visibility (its
                               position, in processing order) and a copy of uvw (24 bytes per
                               row) -- and every call recomputes the visibilities' cell offsets,
@@ -153,7 +158,8 @@ typedef struct wg_plan_info {
                           visibility, when it fits a quarter of the free memory) */
   size_t workspace_bytes; /* device bytes a degrid / grid call allocates */
   double umax, vmax, wmin, wmax; /* |u|, |v| maxima and |w| range in wavelengths */
-  int fft_impl;        /* plane FFT used: 1 cuFFT 2-D, 2 double-float, 3 pruned cuFFT Z2Z */
+  int fft_impl;        /* plane FFT used: 1 cuFFT 2-D, 2 double-float, 3 pruned cuFFT Z2Z,
+                          4 the library's FP32 FFT */
   double rounding_gain; /* factor by which relative plane rounding reaches the result: rms of
                            1 / (n psi_u psi_v psi_w) over the image x (int phi^2)^(3/2) */
   double err_model;    /* predicted eps_rms: kernel term eps_kernel / eps_safety and plane
@@ -320,7 +326,7 @@ int wg_plan_params(int64_t npix_x, int64_t npix_y, double pixsize_x, double pixs
 /* Planner calibration: time the batched 2-D FFT of `batch` n x n planes on the current device,
  * `reps` executions after one warm-up, and return the mean time per plane in milliseconds.
  * impl 1 = cuFFT (C2C for WG_F32, Z2Z for WG_F64), 2 = the library's double-float FFT
- * (WG_F64 only).  Allocates and frees its own device memory; synchronises the device.
+ * (WG_F64 only), 4 = the library's FP32 FFT (WG_F32 only).  Allocates and frees its own device memory; synchronises the device.
  * Errors: WG_ERR_ARG (also for an unsupported size), WG_ERR_OOM, WG_ERR_CUFFT, WG_ERR_CUDA. */
 int wg_fft_time(int64_t n, int precision, int64_t batch, int reps, int impl, double* ms_per_plane);
 
@@ -330,6 +336,15 @@ int wg_fft_time(int64_t n, int precision, int64_t batch, int reps, int impl, dou
  * transform on each call (a utility, not a hot path); synchronises `stream`. */
 int wg_fft2d(void* data, int64_t nu, int64_t nv, int64_t batch, int precision, int impl, int sign,
              void* stream);
+
+/* Shape of the library's FP32 plane FFT (impl 4) for the transforms and plans created after the
+ * call, process-wide: `cols` adjacent columns per CTA in the strided pass (1, 2, 4 or 8; each
+ * row segment a CTA reads is cols x 8 bytes), at most `max_points` line points per CTA (64 ..
+ * 12800; 16 bytes of shared memory each; longer lines run on a cluster of 2, 4 or 8 CTAs) and
+ * `per_thread` points per thread and stage (2 .. 64).  0 keeps an argument's default (4, 12800,
+ * 16).  A calibration knob: results do not depend on it.  Not thread-safe against concurrent
+ * plan creation.  Errors: WG_ERR_ARG for a value out of range (nothing changes). */
+int wg_fft_f32_tune(int cols, int max_points, int per_thread);
 
 /* Arithmetic peak of the current device: FP32 (precision WG_F32) or FP64 (WG_F64) fused
  * multiply-add throughput in flop/s (an FMA counts 2), the best of five timed launches of

@@ -297,17 +297,17 @@ int df64_line_split(int64_t n) {
 
 bool df64_side_ok(int64_t n) { return df64_line_split(n) != 0; }
 
-// The FP32 plane FFT's sides: 1, 2 or 4 CTAs per line with at most kF32SplitAbove points per
-// CTA where the side allows (else up to kF32MaxPart), each part with prime factors 2, 3, 5, 7,
-// 11 only.
+// The FP32 plane FFT's sides: 1, 2, 4 or 8 CTAs per line with at most kF32MaxPart points per
+// CTA, each part with prime factors 2, 3, 5, 7, 11 only.
 bool f32_side_ok(int64_t n) {
+  if (n < 2 || n > kF32MaxSide) return false;
   auto smooth = [](int64_t m) {
     if (m < 2) return false;
     for (int p : {2, 3, 5, 7, 11})
       while (m % p == 0) m /= p;
     return m == 1;
   };
-  for (int s : {1, 2, 4})
+  for (int s : {1, 2, 4, 8})
     if (n % s == 0 && n / s <= kF32MaxPart && smooth(n / s)) return true;
   return false;
 }

@@ -66,10 +66,11 @@ int64_t good_size(int64_t n, int64_t mult);
 
 // Plane FFT implementations.
 enum FftKind { kFftCufft2d = 1, kFftDf64 = 2, kFftPrunedZ2Z = 3, kFftF32 = 4 };
-// The library's FP32 plane FFT: up to kF32MaxPart points per CTA (two lines of complex64 in
-// shared memory); lines above kF32SplitAbove points run on 2 or 4 CTAs.
-constexpr int kF32MaxPart = 8192;
-constexpr int kF32SplitAbove = 4096;
+// The library's FP32 plane FFT: up to kF32MaxPart points per CTA (two buffers of complex64 in
+// shared memory); longer lines run on a cluster of 2, 4 or 8 CTAs.
+constexpr int kF32MaxPart = 12800;
+// sides at most 46340: a plane holds fewer than 2^31 elements (32-bit offsets within a plane)
+constexpr int kF32MaxSide = 46340;
 bool f32_side_ok(int64_t n);
 // The double-float FFT keeps two lines of n complex df64 values in shared memory per CTA
 // (200 KB): sides up to 6400 whose prime factors are 2, 3, 5, 7 and 11 run one line per CTA;

@@ -1156,8 +1156,8 @@ static int fft_util_make(FftUtil& u, int64_t nu, int64_t nv, int64_t batch, int 
   }
   if (impl == 4) {
     if (precision != WG_F32 || !f32_fft_supported(nu, nv))
-      return set_error(WG_ERR_ARG, "the FP32 plane FFT needs WG_F32 and sides with factors 2, 3, 5, "
-                                   "7, 11 of at most 4096 points per CTA part (lines split in 2 or 4)");
+      return set_error(WG_ERR_ARG, "the FP32 plane FFT needs WG_F32 and sides that are 1, 2, 4 or 8 "
+                                   "times a part of at most 12800 points with factors 2, 3, 5, 7, 11");
     cudaError_t e = f32_fft_create(nu, nv, &u.f);
     if (e != cudaSuccess) return set_error(WG_ERR_CUDA, "FP32 FFT setup: %s", cudaGetErrorString(e));
     return WG_OK;
@@ -1200,6 +1200,13 @@ int wg_fft2d(void* data, int64_t nu, int64_t nv, int64_t batch, int precision, i
   cudaStream_t s = (cudaStream_t)stream;
   WG_TRY(fft_util_exec(u, data, batch, precision, sign, s));
   WG_CUDA(cudaStreamSynchronize(s));
+  return WG_OK;
+}
+
+int wg_fft_f32_tune(int cols, int max_points, int per_thread) {
+  if (f32_fft_tune(cols, max_points, per_thread) != 0)
+    return set_error(WG_ERR_ARG, "wg_fft_f32_tune: cols 1, 2, 4 or 8; max_points 64 .. 12800; "
+                                 "per_thread 2 .. 64 (0 keeps a default)");
   return WG_OK;
 }
 

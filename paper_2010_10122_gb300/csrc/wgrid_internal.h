@@ -83,8 +83,10 @@ cudaError_t df64_fft_exec(Df64Fft* f, double2* data, int64_t batch, int sign, cu
 
 // ---- FP32 plane FFT (fft_f32.cu) -------------------------------------------------------
 struct F32Fft;
-int f32_line_split(int64_t n);   // CTAs per line for side n (0: not supported)
+int f32_line_split(int64_t n);   // CTAs per row line for side n (0: not supported)
 bool f32_fft_supported(int64_t nu, int64_t nv);
+// shape of the line kernels for transforms created afterwards (0 keeps a default); -1: invalid
+int f32_fft_tune(int cols, int max_points, int per_thread);
 cudaError_t f32_fft_create(int64_t nu, int64_t nv, F32Fft** out);
 void f32_fft_destroy(F32Fft* f);
 cudaError_t f32_fft_exec(F32Fft* f, float2* data, int64_t batch, int sign, cudaStream_t s,

@@ -104,6 +104,7 @@ SIGNATURES = {
     "wg_fft_time": (_I, [_I64, _I, _I64, _I, _I, ctypes.POINTER(_D)]),
     "wg_fft2d": (_I, [_VP, _I64, _I64, _I64, _I, _I, _I, _VP]),
     "wg_fma_peak": (_I, [_I, ctypes.POINTER(_D)]),
+    "wg_fft_f32_tune": (_I, [_I, _I, _I]),
     "wg_version": (ctypes.c_char_p, []),
 }
 
@@ -484,6 +485,12 @@ def fma_peak(precision="f32") -> float:
     f = ctypes.c_double()
     _check(lib().wg_fma_peak(_prec(precision), ctypes.byref(f)))
     return f.value
+
+
+def fft_f32_tune(cols=0, max_points=0, per_thread=0):
+    """Shape of the library's FP32 plane FFT for transforms and plans created afterwards
+    (wg_fft_f32_tune; 0 keeps a default)."""
+    _check(lib().wg_fft_f32_tune(int(cols), int(max_points), int(per_thread)))
 
 
 def version() -> str:

@@ -63,7 +63,7 @@ def test_df64_split_lines_against_numpy(wg, shape, sign):
                                    (1, 6000, 40), (1, 40, 7056)])
 @pytest.mark.parametrize("sign", [-1, 1])
 def test_f32_fft_matches_cufft_c2c(wg, shape, sign):
-    """The library's FP32 plane FFT (impl 4; lines above 4096 points on 2 or 4 CTAs) against
+    """The library's FP32 plane FFT (impl 4; long lines on clusters of 2, 4 or 8 CTAs) against
     cuFFT's C2C on the same complex64 planes: both round in FP32, so they agree to a few 1e-7
     (normwise)."""
     rng = np.random.default_rng(sum(shape) + 7 * sign)
@@ -77,6 +77,28 @@ def test_f32_fft_matches_cufft_c2c(wg, shape, sign):
     ref = np.fft.fft2(x.astype(np.complex128)) if sign < 0 else \
         np.fft.ifft2(x.astype(np.complex128)) * (shape[1] * shape[2])
     assert np.linalg.norm(a.cpu().numpy() - ref) / np.linalg.norm(ref) < 2e-6
+
+
+@pytest.mark.parametrize("tune", [(4, 256, 8), (2, 64, 2), (8, 12800, 16), (1, 1024, 4),
+                                  (4, 12800, 8)])
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_f32_fft_shapes(wg, tune, sign):
+    """Every shape of the FP32 line kernels gives the same transform: columns per CTA 1, 2, 4, 8,
+    lines on one CTA or split over clusters of 2, 4, 8 CTAs (small part sizes force the splits
+    on small planes), against numpy in FP64."""
+    try:
+        wg.wgrid.fft_f32_tune(*tune)
+        for shape in [(2, 512, 448), (1, 176, 1056), (3, 96, 120)]:
+            rng = np.random.default_rng(sum(shape) + sign)
+            x = (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(np.complex64)
+            a = torch.from_numpy(x).cuda()
+            wg.wgrid.fft2d(a, sign=sign, impl=4)
+            ref = np.fft.fft2(x.astype(np.complex128)) if sign < 0 else \
+                np.fft.ifft2(x.astype(np.complex128)) * (shape[1] * shape[2])
+            err = np.linalg.norm(a.cpu().numpy() - ref) / np.linalg.norm(ref)
+            assert err < 2e-6, (tune, shape, err)
+    finally:
+        wg.wgrid.fft_f32_tune(0, 0, 0)
 
 
 def test_df64_rejects_unsupported(wg):
