@@ -234,3 +234,36 @@ def test_gpu_calls_fail_loudly_without_a_device(wg):
         pytest.skip("a CUDA device is present")
     with pytest.raises(RuntimeError):
         wg.Plan(np.zeros((1, 3)), np.array([1e9]), 64, 64, 1e-4, 1e-4, 1e-5)
+
+
+@pytest.mark.parametrize("bad", [(3, 0, 0), (16, 0, 0), (0, 32, 0), (0, 12801, 0), (0, 0, 1),
+                                 (0, 0, 65), (-1, 0, 0)])
+def test_fft_f32_tune_rejects_out_of_range(wg, bad):
+    """The FP32 FFT's shape knob (host-side only) takes cols 1, 2, 4, 8, max_points 64 .. 12800
+    and per_thread 2 .. 64, and rejects anything else with WG_ERR_ARG."""
+    with pytest.raises(wg.WgridError) as ei:
+        wg.wgrid.fft_f32_tune(*bad)
+    assert ei.value.code == 1
+    wg.wgrid.fft_f32_tune(8, 64, 2)        # extremes are accepted
+    wg.wgrid.fft_f32_tune(1, 12800, 64)
+    wg.wgrid.fft_f32_tune(0, 0, 0)         # back to the defaults
+
+
+def test_planner_f32_library_fft_sides(wg):
+    """fft_impl 4 plans grid sides the FP32 line kernels support: 1, 2, 4 or 8 times a part of at
+    most 12800 points with prime factors 2, 3, 5, 7, 11 (and at most 46340, 32-bit offsets)."""
+    for npix, pix in ((2048, 20), (8192, 4)):
+        _, p = _planner_case(wg, precision="f32", epsilon=1e-5, fft_impl=4, npix_x=npix,
+                             npix_y=npix, pixsize_x=math.radians(pix / 3600),
+                             pixsize_y=math.radians(pix / 3600))
+        assert p["fft_impl"] == 4 and p["nu"] <= 46340
+        ok = False
+        for s in (1, 2, 4, 8):
+            m = p["nu"] // s
+            if p["nu"] % s or m > 12800:
+                continue
+            for f in (2, 3, 5, 7, 11):
+                while m % f == 0:
+                    m //= f
+            ok = ok or m == 1
+        assert ok, p
