@@ -2,11 +2,11 @@
 to csrc/fft_table.inc (run on the target GPU; the library must be built).
 
 Candidates: n = 32 m for 4 <= m <= 512 with m 11-smooth (FFT-friendly multiples of the uv
-tile).  For each n the batched 2-D C2C (FP32) and Z2Z (FP64) cuFFT transforms and the library's
-double-float FFT (FP64 planes; sizes it does not support get 0) are timed through the library's
-wg_fft_time entry point with ~1-2 GiB of planes per batch.  --columns re-measures only some of
-the three columns (c2c, z2z, df64) and --min-n only sizes from there on, keeping the other
-entries of the existing table.  The planner uses the
+tile).  For each n the batched 2-D C2C (FP32) and Z2Z (FP64) cuFFT transforms, the library's
+double-float FFT (FP64 planes) and the library's FP32 FFT (sizes an implementation does not
+support get 0) are timed through the library's wg_fft_time entry point with ~1-2 GiB of planes
+per batch.  --columns re-measures only some of the four columns (c2c, z2z, df64, f32) and
+--min-n only sizes from there on, keeping the other entries of the existing table.  The planner uses the
 table to pick, for each oversampling factor, the fastest size >= sigma * n and to price the
 FFT stage in its cost model (Sec. 4.1).
 
@@ -29,7 +29,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--max-n", type=int, default=16384)
     ap.add_argument("--min-n", type=int, default=0)
-    ap.add_argument("--columns", default="c2c,z2z,df64")
+    ap.add_argument("--columns", default="c2c,z2z,df64,f32")
     ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)),
                                                   "csrc", "fft_table.inc"))
     args = ap.parse_args()
@@ -40,7 +40,7 @@ def main():
             ln = ln.strip()
             if ln.startswith("{"):
                 v = [float(x) for x in ln.strip("{},").split(",")]
-                old[int(v[0])] = v[1:]
+                old[int(v[0])] = (v[1:] + [0.0] * 4)[:4]
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     from paper_2010_10122_gb300 import _build
     _build.build()
@@ -53,8 +53,9 @@ def main():
             continue
         n = 32 * m
         out = [n]
-        for c, (prec, b, impl) in enumerate((("f32", 8, 1), ("f64", 16, 1), ("f64", 16, 2))):
-            name = ("c2c", "z2z", "df64")[c]
+        for c, (prec, b, impl) in enumerate((("f32", 8, 1), ("f64", 16, 1), ("f64", 16, 2),
+                                             ("f32", 8, 4))):
+            name = ("c2c", "z2z", "df64", "f32")[c]
             if (name not in cols or n < args.min_n) and n in old:
                 out.append(old[n][c])
                 continue
@@ -66,14 +67,14 @@ def main():
                 out.append(0.0)
         rows.append(out)
         print(f"n={n:6d} c2c {out[1]*1e3:9.2f} us/plane  z2z {out[2]*1e3:10.2f} us/plane  "
-              f"df64 {out[3]*1e3:10.2f} us/plane", flush=True)
+              f"df64 {out[3]*1e3:10.2f} us/plane  f32 {out[4]*1e3:10.2f} us/plane", flush=True)
     dev = torch.cuda.get_device_name(0)
     with open(args.out, "w") as f:
         f.write(f"// cuFFT batched 2-D plane transform times on {dev}, measured by\n")
         f.write("// paper_2010_10122_gb300/calibrate_fft.py: {n, ms per plane C2C, ms per plane Z2Z, "
-                "ms per plane double-float}\n")
-        for n, a, b, c in rows:
-            f.write(f"{{{n}, {a:.6g}, {b:.6g}, {c:.6g}}},\n")
+                "ms per plane double-float, ms per plane library FP32}\n")
+        for n, a, b, c, d in rows:
+            f.write(f"{{{n}, {a:.6g}, {b:.6g}, {c:.6g}, {d:.6g}}},\n")
     print(f"wrote {len(rows)} sizes to {args.out} in {time.time() - t0:.0f} s")
 
 

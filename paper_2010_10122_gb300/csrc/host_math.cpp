@@ -391,8 +391,7 @@ static double fft_ms_square(int64_t n, int kind, int prec) {
     double a = (double)n * n * std::log2((double)n * n), b = (double)L.n * L.n * std::log2((double)L.n * L.n);
     return ref * a / b * 1.3;   // unmeasured sizes are priced a little higher
   }
-  // the library's FP32 FFT before any calibration: priced above cuFFT's C2C (never chosen
-  // automatically, still plannable when requested)
+  // the library's FP32 FFT at a size beyond the table: priced above cuFFT's C2C
   if (kind == kFftF32) return 2.0 * fft_ms_square(n, kFftCufft2d, prec);
   return std::numeric_limits<double>::infinity();
 }
@@ -444,7 +443,9 @@ static double plan_cost(int prec, int kind, int64_t nu, int64_t nv, int64_t nw, 
                         int64_t nvis, int64_t nx, int64_t npix) {
   double cells = (double)nu * nv;
   double k_cell = prec ? 3.0e-12 : 2.5e-12;   // s per plane cell (screen / (de)grid traffic)
-  double k_pix = prec ? 6.0e-11 : 1.8e-12;    // s per image pixel per plane (screen phase)
+  // s per image pixel per plane (screen phase and accumulation): FP64 in pair arithmetic with an
+  // FP64 anchor every 16 planes (double-float planes), FP64 otherwise; FP32
+  double k_pix = prec ? (kind == kFftDf64 ? 6.0e-12 : 1.2e-11) : 1.8e-12;
   // s per visibility per alpha^2 x lanes; FP64 plans with the double-float FFT (de)grid in pair
   // arithmetic on the FP32 pipes, about twice as fast as FP64 arithmetic
   double k_vis = prec ? (kind == kFftDf64 ? 5.0e-12 : 1.05e-11) : 3.6e-12;
@@ -489,11 +490,13 @@ int choose_plan(const PlanInput& in, PlanParams& out, char* err, int errlen) {
   double nm1_min = -r2 / (1.0 + std::sqrt(1.0 - r2));
   if (in.tile != 0 && in.tile != 16 && in.tile != 32) return fail("tile must be 16 or 32");
 
-  // FFT kinds to consider: FP32 plans use cuFFT C2C; FP64 plans the pruned Z2Z transform or the
-  // double-float FFT, whichever is cheaper among those whose rounding fits epsilon
+  // FFT kinds to consider: FP32 plans use cuFFT C2C (the library's FP32 FFT only on request:
+  // measured slower than cuFFT at the sizes the planner picks, and its pruned time is modelled,
+  // not measured); FP64 plans the pruned Z2Z transform or the double-float FFT, whichever is
+  // cheaper among those whose rounding fits epsilon
   std::vector<int> kinds;
   if (in.fft_impl != 0) kinds.push_back(in.fft_impl);
-  else if (in.prec == 0) { kinds.push_back(kFftCufft2d); kinds.push_back(kFftF32); }
+  else if (in.prec == 0) kinds.push_back(kFftCufft2d);
   else { kinds.push_back(kFftPrunedZ2Z); kinds.push_back(kFftDf64); }
 
   double safety = in.eps_safety > 0 ? in.eps_safety : kDefaultEpsSafety;
