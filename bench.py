@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--serve-vis", default="1e5,5e7")
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
-    ap.add_argument("--serve-loads", default="1.0",
+    ap.add_argument("--serve-loads", default="0.5,0.9",
                     help="Poisson arrival rates as multiples of the one-at-a-time capacity")
     ap.add_argument("--no-serve", action="store_true",
                     help="leave out the bounded serving sub-mix of the default run")
@@ -886,7 +886,7 @@ def main():
             p.close()
         plans = {}
         torch.cuda.empty_cache()
-        serve = serve_benchmark(60, 6, [512, 1024, 2048], (1e5, 2e6), 8, 150.0, [1.0, 2.0],
+        serve = serve_benchmark(60, 6, [512, 1024, 2048], (1e5, 2e6), 8, 150.0, [0.5, 0.9, 2.0],
                                 serial_sample=60)
         serve["sub_mix"] = ("60 requests over 6 observations (512^2 - 2048^2, 1e5 - 2e6 "
                             "visibilities); the full mix runs with bench.py --serve")
