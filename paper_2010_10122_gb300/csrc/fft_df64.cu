@@ -18,6 +18,8 @@
 // doubles into float pairs on load, the pass that writes them joins the pairs back); on the uv
 // side they are complex128 or, for the (de)gridding kernels in pair arithmetic, float pairs.
 // Transforms are unnormalised, forward = e^{-2 pi i}, like cuFFT's.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -246,17 +248,23 @@ k_fft_lines(const __grid_constant__ FftLine L, void* __restrict__ data, int64_t 
       const bool f = fwd != 0;
 #pragma unroll 2
       for (int j = threadIdx.x; j < n; j += T) {
-        cdd x4[4];
+        // output h of the radix-S DFT only (h is the same for the whole CTA)
+        cdd y;
         if (S == 2) {
-          x4[0] = load_elem(g4, base, j);
-          x4[1] = load_elem(g4, base, j + n);
-          dft2(x4);
+          const cdd x0 = load_elem(g4, base, j), x1 = load_elem(g4, base, j + n);
+          y = h == 0 ? c_add(x0, x1) : c_sub(x0, x1);
         } else {
+          cdd x4[4];
 #pragma unroll
           for (int r = 0; r < 4; ++r) x4[r] = load_elem(g4, base, j + r * n);
-          dft4(x4, f);
+          if ((h & 1) == 0) {
+            const cdd t0 = c_add(x4[0], x4[2]), t2 = c_add(x4[1], x4[3]);
+            y = h == 0 ? c_add(t0, t2) : c_sub(t0, t2);
+          } else {
+            const cdd t1 = c_sub(x4[0], x4[2]), t3 = c_mul_mi(c_sub(x4[1], x4[3]), f);
+            y = h == 1 ? c_add(t1, t3) : c_sub(t1, t3);
+          }
         }
-        cdd y = x4[h];
         if (h > 0) y = c_mul(y, twiddle(L.tw2, j * h, f));
         b[swizzle(j, swz)] = store_cdd(y);
       }
@@ -368,6 +376,122 @@ k_fft_lines(const __grid_constant__ FftLine L, void* __restrict__ data, int64_t 
   }
 }
 
+// Split lines on a thread-block cluster of S = L.split CTAs (2 or 4): CTA h copies points
+// [h n, h n + n) of its line into shared memory with asynchronous 16-byte copies (all of them
+// in flight at once; known zeros written directly, doubles split into float pairs in place),
+// the cluster exchanges the parts through distributed shared memory for the radix-S
+// decimation-in-frequency step (CTA h forms only its own y_h, see FftLine), and each CTA then
+// transforms its n points like a one-CTA line and stores the line's outputs S k + h.  The
+// register-path split of k_fft_lines reads all S n points of the line in every CTA with few
+// loads in flight; it remains the fallback when a cluster cannot be launched.
+template <int TMAX, int MINB, bool kAll>
+__global__ void __launch_bounds__(TMAX, MINB)
+k_fft_lines_cluster(const __grid_constant__ FftLine L, void* __restrict__ data, int64_t plane_elems,
+                    int lines_per_plane, int64_t line_stride, int64_t elem_stride, int mode,
+                    int fwd, int split, int skip, int lhalf, int shalf) {
+  namespace cg = cooperative_groups;
+  extern __shared__ __align__(16) float4 fsm[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int n = L.n, S = L.split, nfull = S * n, T = blockDim.x;
+  const int swz = (n & 7) == 0 ? 7 : 0;
+  const bool f = fwd != 0;
+  const int h = (int)cl.block_rank();           // cluster dims (S, 1, 1): blockIdx.x mod S
+  const int64_t lid = blockIdx.x / (unsigned)S;
+  const int64_t plane = lid / lines_per_plane;
+  int line = (int)(lid - plane * lines_per_plane);
+  if (line >= split) line += skip;
+  const int64_t base = plane * plane_elems + (int64_t)line * line_stride;
+  float4* A = fsm;
+  float4* B = fsm + n;
+  const float4* g4 = reinterpret_cast<const float4*>(data);
+  const int i0 = h * n;
+  for (int j = threadIdx.x; j < n; j += T) {
+    const int i = i0 + j;
+    float4* d = A + swizzle(j, swz);
+    if (i < lhalf || i >= nfull - lhalf) cp_async16(d, g4 + base + (int64_t)i * elem_stride);
+    else *d = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  cp_async_commit();
+  cp_async_wait_all();
+  if (mode == 0) {   // doubles in: each split into a float pair in place (the same 16 bytes)
+    for (int j = threadIdx.x; j < n; j += T) {
+      const int i = i0 + j;
+      if (i >= lhalf && i < nfull - lhalf) continue;
+      float4* d = A + swizzle(j, swz);
+      const float4 v = *d;
+      const double2 dv = make_double2(__hiloint2double(__float_as_int(v.y), __float_as_int(v.x)),
+                                      __hiloint2double(__float_as_int(v.w), __float_as_int(v.z)));
+      cdd x; x.r = split_double(dv.x); x.i = split_double(dv.y);
+      *d = store_cdd(x);
+    }
+  }
+  cl.sync();         // every part is in place
+  const float4* P[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) P[r] = cl.map_shared_rank(A, (unsigned)(r < S ? r : 0));
+  for (int j = threadIdx.x; j < n; j += T) {
+    const int off = swizzle(j, swz);
+    cdd y;
+    if (S == 2) {
+      const cdd x0 = load_cdd(P[0][off]), x1 = load_cdd(P[1][off]);
+      y = h == 0 ? c_add(x0, x1) : c_sub(x0, x1);
+    } else {
+      cdd x4[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) x4[r] = load_cdd(P[r][off]);
+      if ((h & 1) == 0) {
+        const cdd t0 = c_add(x4[0], x4[2]), t2 = c_add(x4[1], x4[3]);
+        y = h == 0 ? c_add(t0, t2) : c_sub(t0, t2);
+      } else {
+        const cdd t1 = c_sub(x4[0], x4[2]), t3 = c_mul_mi(c_sub(x4[1], x4[3]), f);
+        y = h == 1 ? c_add(t1, t3) : c_sub(t1, t3);
+      }
+    }
+    if (h > 0) y = c_mul(y, twiddle(L.tw2, j * h, f));
+    B[off] = store_cdd(y);
+  }
+  cl.sync();         // the other CTAs have read this CTA's part: A is free for the stages
+  float4* src = B;
+  float4* dst = A;
+  int Ns = 1;
+  for (int st = 0; st < L.nst; ++st) {
+    const int R = L.radix[st];
+    switch (R) {
+      case 3: stage<3>(src, dst, n, Ns, f, L, swz); break;
+      case 4: stage<4>(src, dst, n, Ns, f, L, swz); break;
+      case 5: stage<5>(src, dst, n, Ns, f, L, swz); break;
+      case 8: stage<8>(src, dst, n, Ns, f, L, swz); break;
+      default:
+        if (kAll) {
+          if (R == 2) stage<2>(src, dst, n, Ns, f, L, swz);
+          else if (R == 7) stage<7>(src, dst, n, Ns, f, L, swz);
+          else stage<11>(src, dst, n, Ns, f, L, swz);
+        }
+        break;
+    }
+    __syncthreads();
+    float4* t = src; src = dst; dst = t;
+    Ns *= R;
+  }
+  // result element i of this CTA is element S i + h of the line
+  if (mode != 1) {
+    float4* out = reinterpret_cast<float4*>(data) + base;
+    for (int i = threadIdx.x; i < n; i += T) {
+      const int o = S * i + h;
+      if (o < shalf || o >= nfull - shalf) out[(int64_t)o * elem_stride] = src[swizzle(i, swz)];
+    }
+  } else {
+    double2* out = reinterpret_cast<double2*>(data) + base;
+    for (int i = threadIdx.x; i < n; i += T) {
+      const int o = S * i + h;
+      if (o >= shalf && o < nfull - shalf) continue;   // not needed downstream
+      const cdd x = load_cdd(src[swizzle(i, swz)]);
+      double2 v; v.x = join_double(x.r); v.y = join_double(x.i);
+      out[(int64_t)o * elem_stride] = v;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------------------
@@ -452,6 +576,12 @@ cudaError_t df64_fft_create(int64_t nu, int64_t nv, Df64Fft** out) {
   WG_SMEM_ATTR(448, 2, false, false, true);  WG_SMEM_ATTR(448, 2, true, false, true);
   WG_SMEM_ATTR(832, 1, false, false, true);  WG_SMEM_ATTR(832, 1, true, false, true);
 #undef WG_SMEM_ATTR
+#define WG_SMEM_ATTR_C(TM, MB, A)                                                                \
+  if (e == cudaSuccess)                                                                          \
+    e = cudaFuncSetAttribute(k_fft_lines_cluster<TM, MB, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax)
+  WG_SMEM_ATTR_C(448, 2, false); WG_SMEM_ATTR_C(448, 2, true);
+  WG_SMEM_ATTR_C(832, 1, false); WG_SMEM_ATTR_C(832, 1, true);
+#undef WG_SMEM_ATTR_C
   if (e != cudaSuccess) {
     if (f->tw_u) cudaFree(f->tw_u);
     if (f->tw_v) cudaFree(f->tw_v);
@@ -492,6 +622,35 @@ static cudaError_t launch_lines(const FftLine& L, double2* data, int64_t batch, 
   bool common = true;   // radices 8, 4, 5, 3 only
   for (int i = 0; i < L.nst; ++i)
     if (L.radix[i] == 2 || L.radix[i] == 7 || L.radix[i] == 11) common = false;
+  if (L.split > 1) {
+    // a cluster of L.split CTAs per line (k_fft_lines_cluster); the register-path split below if
+    // the cluster cannot be launched
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3((unsigned)nlines);
+    cfg.blockDim = dim3((unsigned)L.threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    std::memset(attr, 0, sizeof(attr));
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)L.split;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (nlines > 0x7fffffffLL) return cudaErrorInvalidValue;
+    cudaError_t ec;
+#define WG_CLUSTER(TM, MB, A)                                                                   \
+    ec = cudaLaunchKernelEx(&cfg, k_fft_lines_cluster<TM, MB, A>, L, data, plane,               \
+                            lines_per_plane, line_stride, elem_stride, mode, fwd, split, skip,  \
+                            lhalf, shalf)
+    if (L.threads <= 448) { if (common) WG_CLUSTER(448, 2, false); else WG_CLUSTER(448, 2, true); }
+    else { if (common) WG_CLUSTER(832, 1, false); else WG_CLUSTER(832, 1, true); }
+#undef WG_CLUSTER
+    if (ec == cudaSuccess) return cudaSuccess;
+    cudaGetLastError();   // the launch was refused (no kernel ran): the register-path split
+  }
 #define WG_LINES1(TM, MB, A, Y, P)                                                              \
   k_fft_lines<TM, MB, A, Y, P><<<(unsigned)blocks, L.threads, smem, s>>>(                       \
       L, data, plane, lines_per_plane, line_stride, elem_stride, mode, fwd, split, skip, lhalf, \

@@ -300,21 +300,21 @@ def test_error_model_bounds_measured_error(wg, oracle_lib, sigma):
 
 def test_wide_8k_sampled_fp32(wg, oracle_lib):
     """The 1e8-visibility workload (8192^2 at 4 arcsec, 128 antennas, 64 channels) at
-    eps = 1e-5 in FP32, at full size: 48 sampled visibilities and 12 sampled pixels against
+    eps = 1e-5 in FP32, at full size: 256 sampled visibilities and 32 sampled pixels against
     the oracle (relative L2 over the sample)."""
     obs = S.wide_8k()
     I = S.point_source_image(obs.npix_x, obs.npix_y, seed=0, dtype=np.float32)
     plan = wg.Plan(obs.uvw, obs.freq, obs.npix_x, obs.npix_y, obs.pixsize_x, obs.pixsize_y, 1e-5, "f32")
     vis = plan.degrid(_cu(I)).cpu().numpy()
     rng = np.random.default_rng(0)
-    vsel = rng.choice(obs.nvis, 48, replace=False)
+    vsel = rng.choice(obs.nvis, 256, replace=False)
     rv = oracle_lib.degrid(obs.uvw, obs.freq, I.astype(np.float64), obs.pixsize_x, obs.pixsize_y,
                            vis_index=vsel)
     assert oracle_lib.rel_l2(vis.reshape(-1)[vsel], rv) <= 1e-5
     del vis
     d = S.complex_normal((obs.nrows, obs.nchan), seed=1, dtype=np.complex64)
     img = plan.grid(_cu(d)).cpu().numpy()
-    psel = rng.choice(obs.npix_x * obs.npix_y, 12, replace=False)
+    psel = rng.choice(obs.npix_x * obs.npix_y, 32, replace=False)
     ri = oracle_lib.grid(obs.uvw, obs.freq, d, obs.npix_x, obs.npix_y, obs.pixsize_x,
                          obs.pixsize_y, pixel_index=psel)
     assert oracle_lib.rel_l2(img.reshape(-1)[psel], ri) <= 1e-5
@@ -322,21 +322,21 @@ def test_wide_8k_sampled_fp32(wg, oracle_lib):
 
 def test_wide_8k_sampled_fp64(wg, oracle_lib):
     """The 1e8-visibility workload at eps = 1e-12 in FP64 at full size (the planner's double-float
-    plane FFT on grid sides above 6400, each line on several CTAs): 48 sampled visibilities and
-    12 sampled pixels against the oracle."""
+    plane FFT on grid sides above 6400, each line on several CTAs): 256 sampled visibilities and
+    32 sampled pixels against the oracle."""
     obs = S.wide_8k()
     I = S.point_source_image(obs.npix_x, obs.npix_y, seed=0)
     plan = wg.Plan(obs.uvw, obs.freq, obs.npix_x, obs.npix_y, obs.pixsize_x, obs.pixsize_y, 1e-12, "f64")
     assert plan.info["fft_impl"] == 2 and plan.info["nu"] > 6400, plan.info
     vis = plan.degrid(_cu(I)).cpu().numpy()
     rng = np.random.default_rng(3)
-    vsel = rng.choice(obs.nvis, 48, replace=False)
+    vsel = rng.choice(obs.nvis, 256, replace=False)
     rv = oracle_lib.degrid(obs.uvw, obs.freq, I, obs.pixsize_x, obs.pixsize_y, vis_index=vsel)
     assert oracle_lib.rel_l2(vis.reshape(-1)[vsel], rv) <= 1e-12
     del vis
     d = S.complex_normal((obs.nrows, obs.nchan), seed=1)
     img = plan.grid(_cu(d)).cpu().numpy()
-    psel = rng.choice(obs.npix_x * obs.npix_y, 12, replace=False)
+    psel = rng.choice(obs.npix_x * obs.npix_y, 32, replace=False)
     ri = oracle_lib.grid(obs.uvw, obs.freq, d, obs.npix_x, obs.npix_y, obs.pixsize_x,
                          obs.pixsize_y, pixel_index=psel)
     assert oracle_lib.rel_l2(img.reshape(-1)[psel], ri) <= 1e-12
