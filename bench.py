@@ -256,15 +256,36 @@ def df64_radices(n):
     return r
 
 
-def df64_line_ops(n):
-    """FP32 instructions of one length-n double-float line transform (butterflies and the
-    twiddle products of every stage after the first)."""
+def df64_part_ops(n):
+    """FP32 instructions of one length-n double-float transform held by one CTA (butterflies and
+    the twiddle products of every stage after the first)."""
     ops, ns = 0, 1
     for r in df64_radices(n):
         bf = DF64_BUTTERFLY.get(r, r * (r - 1) * 60)
         ops += (n // r) * (bf + (38 * (r - 1) if ns > 1 else 0))
         ns *= r
     return ops
+
+
+def df64_line_split(n):
+    """CTAs per double-float line, the library's rule: up to 6400 points one CTA, longer lines
+    on a cluster of 2 or 4 CTAs of at most 6400 points each."""
+    if n <= 6400:
+        return 1
+    for s in (2, 4):
+        if n % s == 0 and n // s <= 6400:
+            return s
+    return 0
+
+
+def df64_line_ops(n):
+    """FP32 instructions of one length-n double-float line: one CTA's transform, or for a line
+    on S CTAs the radix-S decimation step (butterfly and S - 1 twiddle products per group of S)
+    and S transforms of n / S points."""
+    S = df64_line_split(n)
+    if S <= 1:
+        return df64_part_ops(n)
+    return (n // S) * (DF64_BUTTERFLY[S] + 38 * (S - 1)) + S * df64_part_ops(n // S)
 
 
 # DRAM bytes the double-float FFT moved per algorithmic byte (one 16-byte read and one 16-byte
@@ -775,7 +796,8 @@ def main():
         peak = 152 * 128 * 2.07e9   # SMs x FP32 lanes x max SM clock, one instruction per lane
         ach = ops / (stage_ms[dom] * 1e-3)
         abytes = nw * df64_fft_bytes(obs.npix_x, obs.npix_y, nu, nv, dir_d)
-        roof = {"bound": "alu", "kernel": "k_fft_lines (double-float plane FFT, row + column pass)",
+        kname = "k_fft_lines_cluster" if df64_line_split(nu) > 1 else "k_fft_lines"
+        roof = {"bound": "alu", "kernel": f"{kname} (double-float plane FFT, row + column pass)",
                 "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s", "frac": ach / peak,
                 "traffic": DF64_DRAM_PER_ALGORITHMIC_BYTE * abytes,
                 "algorithmic_bytes": abytes,

@@ -12,11 +12,23 @@ def test_df64_radix_plan_matches_the_library_rule():
 
 
 def test_df64_line_ops_per_element():
-    # 456 FP32 instructions per element of a 3456-point line (radix-8 butterfly 600, radix 4
-    # 176, radix 3 160, 38 per non-trivial twiddle product)
-    assert bench.df64_line_ops(3456) == 456 * 3456
+    # 456 FP32 instructions per element of a 3456-point transform on one CTA (radix-8 butterfly
+    # 600, radix 4 176, radix 3 160, 38 per non-trivial twiddle product)
+    assert bench.df64_part_ops(3456) == 456 * 3456
     # a single radix-8 stage has no twiddles: one butterfly per 8 elements
+    assert bench.df64_part_ops(8) == 600
     assert bench.df64_line_ops(8) == 600
+    assert bench.df64_line_ops(3456) == 456 * 3456
+    # 13824: four 3456-point parts after a radix-4 decimation step (butterfly 176 and three
+    # twiddle products per group of four)
+    assert bench.df64_line_ops(13824) == 3456 * (176 + 3 * 38) + 4 * 456 * 3456
+
+
+def test_df64_line_split_rule():
+    # one CTA up to 6400 points, else a cluster of 2 or 4 CTAs of at most 6400 points
+    assert bench.df64_line_split(3456) == 1 and bench.df64_line_split(6400) == 1
+    assert bench.df64_line_split(6912) == 2 and bench.df64_line_split(12800) == 2
+    assert bench.df64_line_split(13824) == 4 and bench.df64_line_split(25600) == 4
 
 
 def test_df64_fft_bytes_pruned_and_full():
