@@ -580,7 +580,9 @@ def run_config_1e8(args, wg, dev, hbm_gbs):
     I = S.point_source_image(obs.npix_x, obs.npix_y, seed=0)
     d = S.complex_normal((obs.nrows, obs.nchan), seed=1)
     gen_s = time.perf_counter() - t0
-    vsel, psel = error_sample(obs, 128, 8, seed=2)
+    # 64 pixels: the gridded image's error is largest near the image edge (the 1 / psi
+    # correction amplifies the plane rounding there), so a few pixels estimate it poorly
+    vsel, psel = error_sample(obs, 128, 64, seed=2)
     out = {"workload": "wide_8k", "nvis": obs.nvis, "npix": [obs.npix_x, obs.npix_y],
            "pixsize_arcsec": obs.pixsize_x / S.ARCSEC, "uv_scale": obs.uv_scale,
            "steps": args.steps_1e8, "warmup": 1, "input_generation_s": round(gen_s, 1),
