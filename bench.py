@@ -268,9 +268,19 @@ def df64_part_ops(n):
 
 
 def df64_line_split(n):
-    """CTAs per double-float line, the library's rule: up to 6400 points one CTA, longer lines
-    on a cluster of 2 or 4 CTAs of at most 6400 points each."""
+    """CTAs per double-float line, the library's rule: up to 6400 points one CTA, except that
+    above 2048 a line whose half needs only the radices 8, 4, 5, 3 runs as two halves; longer
+    lines on 2 or 4 CTAs of at most 6400 points (each split line on a thread-block cluster)."""
+    def plan_ok(m):
+        k = m
+        for p in (2, 3, 5, 7, 11):
+            while k % p == 0:
+                k //= p
+        return m >= 2 and k == 1
     if n <= 6400:
+        if n > 2048 and n % 2 == 0 and plan_ok(n // 2) and \
+                not set(df64_radices(n // 2)) & {2, 7, 11}:
+            return 2
         return 1
     for s in (2, 4):
         if n % s == 0 and n // s <= 6400:
@@ -289,9 +299,10 @@ def df64_line_ops(n):
 
 
 # DRAM bytes the double-float FFT moved per algorithmic byte (one 16-byte read and one 16-byte
-# write per cell and pass), measured by ncu on full 3456^2 transforms: 31.1 of 32 B per cell
-# and pass (profiles/k_fft_lines_df64_3456.md); the rest stays in L2 when the kernel ends
-DF64_DRAM_PER_ALGORITHMIC_BYTE = 31.1 / 32.0
+# write per cell and pass), measured by ncu on full 3456^2 transforms (lines as two halves on
+# clusters of 2 CTAs): 30.86 of 32 B per cell and pass (profiles/k_fft_lines_cluster_df64_3456.md);
+# the rest stays in L2 when the kernel ends
+DF64_DRAM_PER_ALGORITHMIC_BYTE = 30.86 / 32.0
 
 
 def df64_fft_bytes(nx, ny, nu, nv, direction):

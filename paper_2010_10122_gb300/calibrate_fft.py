@@ -5,8 +5,8 @@ Candidates: n = 32 m for 4 <= m <= 512 with m 11-smooth (FFT-friendly multiples 
 tile).  For each n the batched 2-D C2C (FP32) and Z2Z (FP64) cuFFT transforms, the library's
 double-float FFT (FP64 planes) and the library's FP32 FFT (sizes an implementation does not
 support get 0) are timed through the library's wg_fft_time entry point with ~1-2 GiB of planes
-per batch.  --columns re-measures only some of the four columns (c2c, z2z, df64, f32) and
---min-n only sizes from there on, keeping the other entries of the existing table.  The planner uses the
+per batch.  --columns re-measures only some of the four columns (c2c, z2z, df64, f32), and
+--min-n / --max-n only the sizes in that range, keeping the other entries of the existing table.  The planner uses the
 table to pick, for each oversampling factor, the fastest size >= sigma * n and to price the
 FFT stage in its cost model (Sec. 4.1).
 
@@ -48,15 +48,19 @@ def main():
     import torch
     rows = []
     t0 = time.time()
-    for m in range(4, args.max_n // 32 + 1):
+    # sizes beyond --max-n (or below --min-n) keep the existing table's entries
+    top = max([args.max_n] + list(old))
+    for m in range(4, top // 32 + 1):
         if not smooth(m):
             continue
         n = 32 * m
+        if n > args.max_n and n not in old:
+            continue
         out = [n]
         for c, (prec, b, impl) in enumerate((("f32", 8, 1), ("f64", 16, 1), ("f64", 16, 2),
                                              ("f32", 8, 4))):
             name = ("c2c", "z2z", "df64", "f32")[c]
-            if (name not in cols or n < args.min_n) and n in old:
+            if (name not in cols or n < args.min_n or n > args.max_n) and n in old:
                 out.append(old[n][c])
                 continue
             batch = max(1, min(64, int((1.5 * 2**30) // (n * n * b))))

@@ -288,7 +288,20 @@ bool df64_line_plan(int64_t n, Df64LinePlan* lp) {
 
 int df64_line_split(int64_t n) {
   Df64LinePlan lp;
-  if (n <= kDf64MaxSide) return df64_line_plan(n, &lp) ? 1 : 0;
+  if (n <= kDf64MaxSide) {
+    // above 2048 points a line runs as two halves on a cluster of 2 CTAs when the half needs
+    // only the common radices 8, 4, 5, 3 (measured on GB300, ms per plane, one CTA -> two:
+    // 3456 0.736 -> 0.709, 4096 1.30 -> 1.00, 6400 3.41 -> 3.03; gridding error at alpha 16,
+    // sigma 1.6 over 256 pixels and three plans 4.4-5.4e-13 -> 3.1-3.4e-13); a half that needs
+    // the generic radices 7, 11 or a radix 2 keeps one CTA per line (2816: 0.79 -> 0.87)
+    if (n > 2048 && n % 2 == 0 && df64_line_plan(n / 2, &lp)) {
+      bool common = true;
+      for (int i = 0; i < lp.nst; ++i)
+        if (lp.radix[i] == 2 || lp.radix[i] == 7 || lp.radix[i] == 11) common = false;
+      if (common) return 2;
+    }
+    return df64_line_plan(n, &lp) ? 1 : 0;
+  }
   if (n > kDf64MaxSplitSide) return 0;
   for (int s : {2, 4})
     if (n % s == 0 && n / s <= kDf64MaxSide) return df64_line_plan(n / s, &lp) ? s : 0;

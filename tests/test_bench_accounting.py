@@ -18,15 +18,23 @@ def test_df64_line_ops_per_element():
     # a single radix-8 stage has no twiddles: one butterfly per 8 elements
     assert bench.df64_part_ops(8) == 600
     assert bench.df64_line_ops(8) == 600
-    assert bench.df64_line_ops(3456) == 456 * 3456
+    # a 3456-point line runs as two 1728-point halves (radices 8, 8, 3, 3, 3: 419.25 per element)
+    # after one radix-2 decimation step (butterfly 44 and one twiddle product per pair)
+    assert bench.df64_part_ops(1728) == 724464
+    assert bench.df64_line_ops(3456) == 1728 * (44 + 38) + 2 * 724464
     # 13824: four 3456-point parts after a radix-4 decimation step (butterfly 176 and three
     # twiddle products per group of four)
     assert bench.df64_line_ops(13824) == 3456 * (176 + 3 * 38) + 4 * 456 * 3456
 
 
 def test_df64_line_split_rule():
-    # one CTA up to 6400 points, else a cluster of 2 or 4 CTAs of at most 6400 points
-    assert bench.df64_line_split(3456) == 1 and bench.df64_line_split(6400) == 1
+    # two halves above 2048 points when the half needs only the radices 8, 4, 5, 3
+    assert bench.df64_line_split(3456) == 2 and bench.df64_line_split(4096) == 2
+    assert bench.df64_line_split(6400) == 2
+    assert bench.df64_line_split(2048) == 1           # not above 2048
+    assert bench.df64_line_split(2816) == 1           # half 1408 = 2^7 x 11: generic radix 11
+    assert bench.df64_line_split(3360) == 1           # half 1680 has a factor 7
+    # longer lines: 2 or 4 CTAs of at most 6400 points
     assert bench.df64_line_split(6912) == 2 and bench.df64_line_split(12800) == 2
     assert bench.df64_line_split(13824) == 4 and bench.df64_line_split(25600) == 4
 
