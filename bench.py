@@ -230,8 +230,10 @@ def algorithmic_flops_per_vis(alpha):
 # FP32 arithmetic instructions of the double-float FFT (paper_2010_10122_gb300/csrc/fft_df64.cu),
 # counted from its operations: double-float add 11 (two-sum 6, two adds, renormalisation 3),
 # product 7, complex add 22, scale by a constant 14, twiddle product 38 (two fused two-product
-# sums of 19); butterflies: radix 2 44, 3 160, 4 176, 5 464, 8 600, generic R (7, 11) R(R-1) x 60.
-DF64_BUTTERFLY = {2: 44, 3: 160, 4: 176, 5: 464, 8: 600}
+# sums of 19), fused multiply-add 15; butterflies: radix 2 44, 3 160, 4 176, 5 464, 8 600, and
+# the symmetric odd radices R = 7, 11 (P = (R - 1) / 2: (R - 1) + P complex adds, then per output
+# pair 4 P fused multiply-adds and 2 complex adds) 870 and 2050.
+DF64_BUTTERFLY = {2: 44, 3: 160, 4: 176, 5: 464, 7: 870, 8: 600, 11: 2050}
 
 
 def df64_radices(n):
@@ -261,7 +263,7 @@ def df64_part_ops(n):
     the twiddle products of every stage after the first)."""
     ops, ns = 0, 1
     for r in df64_radices(n):
-        bf = DF64_BUTTERFLY.get(r, r * (r - 1) * 60)
+        bf = DF64_BUTTERFLY[r]
         ops += (n // r) * (bf + (38 * (r - 1) if ns > 1 else 0))
         ns *= r
     return ops

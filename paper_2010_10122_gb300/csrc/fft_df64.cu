@@ -36,6 +36,8 @@ struct DftConst {
   dd c51, c52;       // cos(2 pi / 5), cos(4 pi / 5)
   dd s51, s52;       // sin(2 pi / 5), sin(4 pi / 5)
   dd r2;             // sqrt(2) / 2
+  dd c7[3], s7[3];   // cos, sin (2 pi k / 7), k = 1 .. 3
+  dd c11[5], s11[5]; // cos, sin (2 pi k / 11), k = 1 .. 5
 };
 
 constexpr int kMaxStages = 24;
@@ -121,30 +123,55 @@ __device__ __forceinline__ void dft5(cdd* x, bool fwd, const DftConst& k) {
   x[2] = c_add(a2, ib2);
   x[3] = c_sub(a2, ib2);
 }
-// generic radix r (7, 11): y_q = sum_k x_k W_n^{k q n / r}
+// odd radix R (7, 11): with a_k = x_k + x_{R-k} and b_k = x_k - x_{R-k} (k = 1 .. P = (R - 1) / 2),
+//   y_q = x_0 + sum_k a_k cos(2 pi k q / R) -/+ i sum_k b_k sin(2 pi k q / R),
+// and y_{R-q} the same with the other sign of the sine sum (forward: minus for y_q); the sums
+// are chains of dd_fma against the pair constants (4 P^2 of them instead of the (R - 1)^2
+// complex products of a plain DFT)
 template <int R>
-__device__ __forceinline__ void dft_generic(cdd* x, bool fwd, const float4* __restrict__ tw, int n) {
-  cdd y[R];
-  const int step = n / R;
+__device__ __forceinline__ void dft_odd(cdd* x, bool fwd, const dd* cs, const dd* sn) {
+  constexpr int P = (R - 1) / 2;
+  cdd a[P], b[P];
 #pragma unroll
-  for (int q = 0; q < R; ++q) {
-    cdd acc = x[0];
-#pragma unroll
-    for (int kk = 1; kk < R; ++kk) acc = c_add(acc, c_mul(x[kk], twiddle(tw, ((kk * q) % R) * step, fwd)));
-    y[q] = acc;
+  for (int k = 1; k <= P; ++k) {
+    a[k - 1] = c_add(x[k], x[R - k]);
+    b[k - 1] = c_sub(x[k], x[R - k]);
   }
+  cdd y0 = x[0];
 #pragma unroll
-  for (int q = 0; q < R; ++q) x[q] = y[q];
+  for (int k = 0; k < P; ++k) y0 = c_add(y0, a[k]);
+#pragma unroll
+  for (int q = 1; q <= P; ++q) {
+    cdd re = x[0], im;
+    im.r = dd_make(0.f, 0.f);
+    im.i = im.r;
+#pragma unroll
+    for (int k = 1; k <= P; ++k) {
+      const int m = (k * q) % R;
+      const int mm = m <= P ? m : R - m;
+      const dd c = cs[mm - 1];
+      const dd sv = m <= P ? sn[mm - 1] : dd_neg(sn[mm - 1]);
+      re.r = dd_fma(a[k - 1].r, c, re.r);
+      re.i = dd_fma(a[k - 1].i, c, re.i);
+      im.r = dd_fma(b[k - 1].r, sv, im.r);
+      im.i = dd_fma(b[k - 1].i, sv, im.i);
+    }
+    const cdd mi = c_mul_mi(im, true);   // -i im
+    x[q] = fwd ? c_add(re, mi) : c_sub(re, mi);
+    x[R - q] = fwd ? c_sub(re, mi) : c_add(re, mi);
+  }
+  x[0] = y0;
 }
 
 template <int R>
 __device__ __forceinline__ void butterfly(cdd* x, bool fwd, const FftLine& L) {
-  if (R == 2) dft2(x);
-  else if (R == 3) dft3(x, fwd, L.k);
-  else if (R == 4) dft4(x, fwd);
-  else if (R == 5) dft5(x, fwd, L.k);
-  else if (R == 8) dft8(x, fwd, L.k);
-  else dft_generic<R>(x, fwd, L.tw, L.n);
+  if constexpr (R == 2) dft2(x);
+  else if constexpr (R == 3) dft3(x, fwd, L.k);
+  else if constexpr (R == 4) dft4(x, fwd);
+  else if constexpr (R == 5) dft5(x, fwd, L.k);
+  else if constexpr (R == 8) dft8(x, fwd, L.k);
+  else if constexpr (R == 7) dft_odd<7>(x, fwd, L.k.c7, L.k.s7);
+  else dft_odd<11>(x, fwd, L.k.c11, L.k.s11);
 }
 
 
@@ -555,6 +582,14 @@ static cudaError_t make_line(int nline, FftLine* L, float4** tw) {
   L->k.s51 = host_dd(sinl(2 * pi / 5));
   L->k.s52 = host_dd(sinl(4 * pi / 5));
   L->k.r2 = host_dd(sqrtl(2.0L) / 2);
+  for (int q = 1; q <= 3; ++q) {
+    L->k.c7[q - 1] = host_dd(cosl(2 * pi * q / 7));
+    L->k.s7[q - 1] = host_dd(sinl(2 * pi * q / 7));
+  }
+  for (int q = 1; q <= 5; ++q) {
+    L->k.c11[q - 1] = host_dd(cosl(2 * pi * q / 11));
+    L->k.s11[q - 1] = host_dd(sinl(2 * pi * q / 11));
+  }
   return cudaSuccess;
 }
 

@@ -415,11 +415,13 @@ static double fft_ms_square(int64_t n, int kind, int prec) {
 // per line) and the pruned loads / stores of its row pass leave 0.15 + 0.85 x the image
 // fraction of the full transform (measured on GB300: 0.542 ms for a 3456^2 plane with a 2048^2
 // image, against 0.828 ms for the full transform).
-static double fft_ms(int64_t nu, int64_t nv, int kind, int prec, int64_t nx) {
+static double fft_ms(int64_t nu, int64_t nv, int kind, int prec, int64_t nx, int64_t ny) {
   double cu = fft_ms_square(nu, kind, prec) / ((double)nu * nu);
   double cv = fft_ms_square(nv, kind, prec) / ((double)nv * nv);
   double full = 0.5 * (cu + cv) * (double)nu * nv;
-  const double frac = std::min(1.0, (double)nx / (double)nu);
+  // image fraction of a side, the geometric mean over the two (square planes: nx / nu); a single
+  // side's fraction would favour a plane longer in that direction
+  const double frac = std::min(1.0, std::sqrt((double)nx / (double)nu * (double)ny / (double)nv));
   if (kind == kFftPrunedZ2Z) return full * (0.5 + 0.5 * frac) * 1.07;   // 1-D plans: 7 % overhead
   if (kind == kFftDf64) return full * (0.15 + 0.85 * frac);
   // FP32 FFT (memory-bound): the pruned passes move (1 + f)^2 / 4 of the full transform's
@@ -453,7 +455,7 @@ static std::vector<int64_t> size_candidates(int64_t nmin, int64_t mult, int kind
 // stage times of this library on GB300 (2048^2 image, 1e6 visibilities, alpha = G = 8 in FP32
 // and 16 in FP64) divided by the units processed.
 static double plan_cost(int prec, int kind, int64_t nu, int64_t nv, int64_t nw, int alpha,
-                        int64_t nvis, int64_t nx, int64_t npix) {
+                        int64_t nvis, int64_t nx, int64_t ny) {
   double cells = (double)nu * nv;
   double k_cell = prec ? 3.0e-12 : 2.5e-12;   // s per plane cell (screen / (de)grid traffic)
   // s per image pixel per plane (screen phase and accumulation): FP64 in pair arithmetic with an
@@ -464,19 +466,19 @@ static double plan_cost(int prec, int kind, int64_t nu, int64_t nv, int64_t nw, 
   double k_vis = prec ? (kind == kFftDf64 ? 5.0e-12 : 1.05e-11) : 3.6e-12;
   const int G = alpha <= 4 ? 4 : (alpha <= 8 ? 8 : 16);
   const double lanes = prec ? 0.5 * (G + alpha) : (double)G;
-  return nw * (1e-3 * fft_ms(nu, nv, kind, prec, nx) + cells * k_cell + (double)npix * k_pix) +
+  return nw * (1e-3 * fft_ms(nu, nv, kind, prec, nx, ny) + cells * k_cell + (double)(nx * ny) * k_pix) +
          (double)nvis * alpha * alpha * lanes * k_vis;
 }
 
 // Cheapest (nu, nv) for one plane among the candidates (FFT + traffic per cell); false if the
 // FFT kind supports none.
 static bool choose_grid(int64_t nmin_u, int64_t nmin_v, int prec, int kind, int64_t mult,
-                        int64_t nx, int64_t* nu, int64_t* nv) {
+                        int64_t nx, int64_t ny, int64_t* nu, int64_t* nv) {
   double k_cell = prec ? 3.0e-12 : 2.5e-12;
   double best = std::numeric_limits<double>::infinity();
   for (int64_t a : size_candidates(nmin_u, mult, kind))
     for (int64_t b : size_candidates(nmin_v, mult, kind)) {
-      double c = 1e-3 * fft_ms(a, b, kind, prec, nx) + k_cell * (double)a * b;
+      double c = 1e-3 * fft_ms(a, b, kind, prec, nx, ny) + k_cell * (double)a * b;
       if (c < best) { best = c; *nu = a; *nv = b; }
     }
   return std::isfinite(best);
@@ -548,7 +550,7 @@ int choose_plan(const PlanInput& in, PlanParams& out, char* err, int errlen) {
         int64_t minn = std::max<int64_t>(2 * alpha, 16);
         if (!choose_grid(std::max<int64_t>((int64_t)std::ceil(p.sigma * in.nx), minn),
                          std::max<int64_t>((int64_t)std::ceil(p.sigma * in.ny), minn), in.prec,
-                         kind, tile, in.nx, &p.nu, &p.nv))
+                         kind, tile, in.nx, in.ny, &p.nu, &p.nv))
           break;   // larger sigma only needs larger grids
         size_ok = true;
         p.ntu = p.nu / tile; p.ntv = p.nv / tile;
@@ -583,8 +585,7 @@ int choose_plan(const PlanInput& in, PlanParams& out, char* err, int errlen) {
         double e_r = plane_rounding(kind, in.prec, p.nu, p.nv) * p.gain;
         p.err_model = std::sqrt(e_k * e_k + e_r * e_r);
         if (in.force_sigma <= 0 && p.err_model > in.eps) continue;
-        p.cost = plan_cost(in.prec, kind, p.nu, p.nv, p.nw, alpha, in.nvis, in.nx,
-                           in.nx * in.ny);
+        p.cost = plan_cost(in.prec, kind, p.nu, p.nv, p.nw, alpha, in.nvis, in.nx, in.ny);
         if (p.cost < best.cost) { best = p; found = true; }
         break;
       }

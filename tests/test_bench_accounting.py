@@ -15,6 +15,10 @@ def test_df64_line_ops_per_element():
     # 456 FP32 instructions per element of a 3456-point transform on one CTA (radix-8 butterfly
     # 600, radix 4 176, radix 3 160, 38 per non-trivial twiddle product)
     assert bench.df64_part_ops(3456) == 456 * 3456
+    # the symmetric odd radices: (R - 1) + P complex adds (22 each), then per output pair 4 P
+    # fused multiply-adds (15) and 2 complex adds, P = (R - 1) / 2
+    for r, p in ((7, 3), (11, 5)):
+        assert bench.DF64_BUTTERFLY[r] == 22 * (r - 1 + p) + p * (4 * p * 15 + 44)
     # a single radix-8 stage has no twiddles: one butterfly per 8 elements
     assert bench.df64_part_ops(8) == 600
     assert bench.df64_line_ops(8) == 600
