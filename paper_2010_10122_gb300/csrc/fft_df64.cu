@@ -8,12 +8,14 @@
 // transform is ~5e-15 relative (vs ~2e-16 for FP64); the planner accounts for it (its
 // rounding is amplified by the 1 / psi correction, see plane_rounding / rounding_gain).
 //
-// Algorithm: each 1-D transform is a mixed-radix (8 and 4 for the power of two, 5, 3, a
-// generic radix for 7 / 11, 2 only for n = 2 * odd) Stockham autosort FFT run by one CTA per
+// Algorithm: each 1-D transform is a mixed-radix (8 and 4 for the power of two, 5, 3, the
+// symmetric 7 and 11, 2 only for n = 2 * odd) Stockham autosort FFT run by one CTA per
 // line with about n / 8 threads (one radix-8 butterfly each) over two n-element shared-memory
 // buffers (ping-pong); up to n = 3584 two CTAs share an SM.  A pass that reads float pairs in
 // full runs persistent CTAs instead, which copy their next line into the free buffer (cp.async)
-// while storing the current one.  The 2-D plane transform is a pass over rows (contiguous) and a
+// while storing the current one.  Lines above 6400 points, and lines above 2048 whose half needs
+// only the radices 8, 4, 5, 3, run on a thread-block cluster of 2 or 4 CTAs
+// (k_fft_lines_cluster).  The 2-D plane transform is a pass over rows (contiguous) and a
 // pass over columns.  On the image side planes are complex128 (the pass that reads them splits
 // doubles into float pairs on load, the pass that writes them joins the pairs back); on the uv
 // side they are complex128 or, for the (de)gridding kernels in pair arithmetic, float pairs.
