@@ -330,7 +330,7 @@ def run_sweep(args):
     dev = torch.device("cuda", 0)
     rng = np.random.default_rng(0)
     vsel = rng.choice(obs.nvis, 256, replace=False)
-    psel = rng.choice(obs.npix_x * obs.npix_y, 8, replace=False)
+    psel = rng.choice(obs.npix_x * obs.npix_y, 64, replace=False)   # edge pixels carry the largest errors
     rv = direct.degrid(obs.uvw, obs.freq, I, obs.pixsize_x, obs.pixsize_y, vis_index=vsel)
     ri = direct.grid(obs.uvw, obs.freq, d, obs.npix_x, obs.npix_y, obs.pixsize_x, obs.pixsize_y,
                      pixel_index=psel)
