@@ -301,8 +301,10 @@ def test_error_model_bounds_measured_error(wg, oracle_lib, sigma):
 
 def test_wide_8k_sampled_fp32(wg, oracle_lib):
     """The 1e8-visibility workload (8192^2 at 4 arcsec, 128 antennas, 64 channels) at
-    eps = 1e-5 in FP32, at full size: 256 sampled visibilities and 32 sampled pixels against
-    the oracle (relative L2 over the sample)."""
+    eps = 1e-5 in FP32, at full size: 256 sampled visibilities and 256 sampled pixels against
+    the oracle (relative L2 over the sample; the gridded error is largest near the image edge,
+    so the pixel sample must be large: over 256 uniform pixels three plans measured 5.4e-6 -
+    5.6e-6, pixels within 64 of the edge about 1e-5)."""
     obs = S.wide_8k()
     I = S.point_source_image(obs.npix_x, obs.npix_y, seed=0, dtype=np.float32)
     plan = wg.Plan(obs.uvw, obs.freq, obs.npix_x, obs.npix_y, obs.pixsize_x, obs.pixsize_y, 1e-5, "f32")
@@ -315,7 +317,7 @@ def test_wide_8k_sampled_fp32(wg, oracle_lib):
     del vis
     d = S.complex_normal((obs.nrows, obs.nchan), seed=1, dtype=np.complex64)
     img = plan.grid(_cu(d)).cpu().numpy()
-    psel = rng.choice(obs.npix_x * obs.npix_y, 32, replace=False)
+    psel = rng.choice(obs.npix_x * obs.npix_y, 256, replace=False)
     ri = oracle_lib.grid(obs.uvw, obs.freq, d, obs.npix_x, obs.npix_y, obs.pixsize_x,
                          obs.pixsize_y, pixel_index=psel)
     assert oracle_lib.rel_l2(img.reshape(-1)[psel], ri) <= 1e-5
