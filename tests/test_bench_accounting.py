@@ -61,3 +61,25 @@ def test_gridding_flops_per_visibility():
     # alpha + 3 (2 flops per step)
     for a in (4, 8, 15, 16):
         assert bench.algorithmic_flops_per_vis(a) == 4 * a ** 3 + 6 * a * (a + 3)
+
+
+def test_stratified_pixel_sample():
+    """The stratified image-error estimate: the edge stratum first, then the interior; with every
+    pixel of both strata in the sample it is exactly the image's relative L2 error."""
+    import numpy as np
+    nx, ny, band = 40, 24, 5
+    psel, nb, share = bench.stratified_pixels(nx, ny, seed=3, band=band, nb=50, ni=30)
+    jx, jy = psel // ny, psel % ny
+    edge = np.minimum(np.minimum(jx, nx - 1 - jx), np.minimum(jy, ny - 1 - jy))
+    assert len(psel) == 80 and nb == 50 and len(set(psel.tolist())) == 80
+    assert (edge[:nb] < band).all() and (edge[nb:] >= band).all()
+    n_band = nx * ny - (nx - 2 * band) * (ny - 2 * band)
+    assert share == n_band / (nx * ny)
+    # every pixel sampled: the estimate is the plain relative L2 over the image
+    all_idx, nb_all, share_all = bench.stratified_pixels(nx, ny, seed=0, band=band, nb=10 ** 6, ni=10 ** 6)
+    assert nb_all == n_band and len(all_idx) == nx * ny
+    rng = np.random.default_rng(1)
+    ref = rng.standard_normal(nx * ny)
+    x = ref + 1e-3 * rng.standard_normal(nx * ny) * (1 + 9 * (np.arange(nx * ny) % 7 == 0))
+    est = bench.stratified_rel_l2(x[all_idx], ref[all_idx], nb_all, share_all)
+    assert abs(est - np.linalg.norm(x - ref) / np.linalg.norm(ref)) < 1e-12 * est
