@@ -368,9 +368,12 @@ double rounding_gain(const PolyKernel& K, const std::vector<double>& psi_c, int6
 double plane_rounding(int kind, int prec, int64_t nu, int64_t nv) {
   // unit roundoff of the plane arithmetic.  c: on GB300 (2048^2 image, 1e6 visibilities,
   // alpha 16, sigma 1.5 - 2.0, gain 880 - 2.7) the double-float planes added a degrid error of
-  // (4.0 - 6.1)e-15 x gain, i.e. c = 0.024 - 0.037 at 3200^2; 0.06 leaves a margin
+  // (4.0 - 6.1)e-15 x gain, i.e. c = 0.024 - 0.037 at 3200^2; the gridded image's error, taken
+  // over the whole image (a stratified pixel sample that weights the edge band, where the
+  // correction amplifies the rounding most), reached c = 0.062 at sigma 1.45 (gain ~1600);
+  // 0.065 bounds both
   double u = kind == kFftDf64 ? 0x1p-47 : (prec ? 0x1p-53 : 0x1p-24);   // kFftF32: FP32
-  const double c = 0.06;
+  const double c = 0.065;
   return c * u * std::log2((double)nu * (double)nv);
 }
 
