@@ -163,7 +163,8 @@ typedef struct wg_plan_info {
   double rounding_gain; /* factor by which relative plane rounding reaches the result: rms of
                            1 / (n psi_u psi_v psi_w) over the image x (int phi^2)^(3/2) */
   double err_model;    /* predicted eps_rms: kernel term eps_kernel / eps_safety and plane
-                          rounding term (unit roundoff x 0.065 log2(nu nv) x rounding_gain),
+                          rounding term (unit roundoff x c log2(nu nv) x rounding_gain, c = 0.065 (1 +
+                          rounding_gain / 2000)),
                           added in quadrature; the planner keeps it <= epsilon unless sigma
                           is forced */
 } wg_plan_info;

@@ -366,16 +366,19 @@ double rounding_gain(const PolyKernel& K, const std::vector<double>& psi_c, int6
 }
 
 double plane_rounding(int kind, int prec, int64_t nu, int64_t nv) {
-  // unit roundoff of the plane arithmetic.  c: on GB300 (2048^2 image, 1e6 visibilities,
-  // alpha 16, sigma 1.5 - 2.0, gain 880 - 2.7) the double-float planes added a degrid error of
-  // (4.0 - 6.1)e-15 x gain, i.e. c = 0.024 - 0.037 at 3200^2; the gridded image's error, taken
-  // over the whole image (a stratified pixel sample that weights the edge band, where the
-  // correction amplifies the rounding most), reached c = 0.062 at sigma 1.45 (gain ~1600);
-  // 0.065 bounds both
+  // unit roundoff of the plane arithmetic; the caller multiplies by the rounding gain
   double u = kind == kFftDf64 ? 0x1p-47 : (prec ? 0x1p-53 : 0x1p-24);   // kFftF32: FP32
-  const double c = 0.065;
-  return c * u * std::log2((double)nu * (double)nv);
+  return u * std::log2((double)nu * (double)nv);
 }
+
+// Coefficient of the rounding term at rounding gain G.  Measured on GB300 (2048^2 image, 1e6
+// visibilities, alpha 16, double-float planes): the degrid error added (4.0 - 6.1)e-15 x G over
+// sigma 1.5 - 2.0 (G 880 - 2.7), i.e. c = 0.024 - 0.037; the gridded image's error over the
+// whole image (a stratified pixel sample weighting the edge band, where the correction
+// amplifies the rounding most) varies from plan to plan (the summation order inside a bin
+// differs) and reached c = 0.043 at G 290, 0.081 at G 880 and 0.062 at G 1600.  The spread
+// widens with G, so the coefficient does: 0.065 (1 + G / 2000).
+double rounding_coefficient(double gain) { return 0.065 * (1.0 + gain / 2000.0); }
 
 // Measured plane-transform times on GB300, written by calibrate_fft.py: batched cuFFT 2-D C2C
 // and Z2Z, the library's double-float FFT and its FP32 FFT (0 where not measured or not
@@ -585,7 +588,7 @@ int choose_plan(const PlanInput& in, PlanParams& out, char* err, int errlen) {
         p.gain = rounding_gain(K, pc, in.nx, in.ny, in.psx, in.psy, p.nu, p.nv, in.do_w,
                                p.nshift, p.dw);
         double e_k = p.eps_kernel / safety;
-        double e_r = plane_rounding(kind, in.prec, p.nu, p.nv) * p.gain;
+        double e_r = rounding_coefficient(p.gain) * plane_rounding(kind, in.prec, p.nu, p.nv) * p.gain;
         p.err_model = std::sqrt(e_k * e_k + e_r * e_r);
         if (in.force_sigma <= 0 && p.err_model > in.eps) continue;
         p.cost = plan_cost(in.prec, kind, p.nu, p.nv, p.nw, alpha, in.nvis, in.nx, in.ny);

@@ -105,7 +105,8 @@ double rounding_gain(const PolyKernel& K, const std::vector<double>& psi_c, int6
 // Relative normwise rounding of one plane transform (and the arithmetic around it) of the
 // given kind and precision on an nu x nv grid: c * u * log2(nu nv), with u the unit roundoff
 // (FP32 2^-24, FP64 2^-53, double-float 2^-47) and c fitted on GB300 measurements.
-double plane_rounding(int kind, int prec, int64_t nu, int64_t nv);
+double plane_rounding(int kind, int prec, int64_t nu, int64_t nv);   // u log2(nu nv)
+double rounding_coefficient(double gain);                              // c(G) of the rounding term
 
 struct PlanInput {
   int64_t nx, ny;

@@ -170,9 +170,11 @@ def test_rounding_gain_matches_its_definition(wg, prec, eps, impl):
                           info["nv"], info["alpha"], info["beta"], info["mu"], info["nshift"],
                           info["dw"])
     assert info["rounding_gain"] == pytest.approx(ref, rel=2e-3)
-    # the planner's rounding term: c u log2(nu nv) G, u the unit roundoff of the plane arithmetic
+    # the planner's rounding term: c(G) u log2(nu nv) G, u the unit roundoff of the plane
+    # arithmetic, c(G) = 0.065 (1 + G / 2000)
     u = {1: 2.0 ** -24 if prec == "f32" else 2.0 ** -53, 2: 2.0 ** -47, 3: 2.0 ** -53}[info["fft_impl"]]
-    r = 0.065 * u * math.log2(info["nu"] * info["nv"]) * info["rounding_gain"]
+    g = info["rounding_gain"]
+    r = 0.065 * (1 + g / 2000) * u * math.log2(info["nu"] * info["nv"]) * g
     k = info["eps_kernel"] / 0.8
     assert info["err_model"] == pytest.approx(math.hypot(k, r), rel=1e-12)
 
