@@ -309,24 +309,14 @@ class CudaExecutor(Executor):
         # cached workspace beyond what the slots can use at once goes back to the driver first,
         # so that it does not crowd out the plan
         self.wg.pool_trim(len(self.streams) * self.cap, device=self.device)
-        # the cap is a per-request target: an observation whose single w-plane (with its
-        # per-visibility partial sums and records) needs more gets twice the cap, up to a
-        # quarter of the device; the server admits it by the workspace the plan reports
-        cap = self.cap
-        limit = max(cap, self.torch.cuda.get_device_properties(self.device).total_memory // 4)
-        while True:
-            try:
-                with self.torch.cuda.device(self.device):
-                    p = self.wg.Plan(o.uvw, o.freq, o.npix_x, o.npix_y, o.pixsize_x,
-                                     o.pixsize_y, epsilon, precision, max_workspace=cap,
-                                     device=self.device, stream=self.plan_stream,
-                                     compact_index=self.compact)
-                break
-            except self.wg.WgridError as e:
-                if e.code != self.wg.WG_ERR_OOM or "above the cap" not in str(e) \
-                        or cap == 0 or cap >= limit:
-                    raise
-                cap = min(2 * cap, limit)
+        limit = max(self.cap, self.torch.cuda.get_device_properties(self.device).total_memory // 4)
+
+        def make(cap):
+            with self.torch.cuda.device(self.device):
+                return self.wg.Plan(o.uvw, o.freq, o.npix_x, o.npix_y, o.pixsize_x, o.pixsize_y,
+                                    epsilon, precision, max_workspace=cap, device=self.device,
+                                    stream=self.plan_stream, compact_index=self.compact)
+        p = plan_with_cap_target(make, self.cap, limit, self.wg.WgridError, self.wg.WG_ERR_OOM)
         with self._lock:
             self.plans[key] = p
         info = p.info
@@ -397,6 +387,22 @@ class CudaExecutor(Executor):
 
     def finish(self, req, handle):
         req.result = handle[1] if self.keep_results else None
+
+
+def plan_with_cap_target(make: Callable[[int], Any], cap: int, limit: int, error_type,
+                         oom_code: int) -> Any:
+    """make(cap) with the workspace cap as a per-request target: an observation whose single
+    w-plane (with its per-visibility partial sums and records) needs more than the cap gets
+    twice the cap, and so on up to `limit`; the server then admits the plan by the workspace it
+    reports.  Other errors, and the cap error at the limit (or with no cap), are raised."""
+    while True:
+        try:
+            return make(cap)
+        except error_type as e:
+            if getattr(e, "code", None) != oom_code or "above the cap" not in str(e) \
+                    or cap == 0 or cap >= limit:
+                raise
+            cap = min(2 * cap, limit)
 
 
 def run_serial(executor: Executor, requests: List[Request]) -> float:

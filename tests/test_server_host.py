@@ -178,3 +178,45 @@ def test_stuck_request_times_out_on_the_host():
     srv = Server(ex, slots=2, memory_budget=100, timeout_s=0.5, clock=clk)
     with pytest.raises(ServerTimeout):
         srv.run(make(1, "stuck"))
+
+
+def test_workspace_cap_is_a_target_host():
+    """plan_with_cap_target doubles the cap while the plan reports that one w-plane needs more,
+    up to the limit; other errors and the cap error at the limit are raised unchanged."""
+    from paper_2010_10122_gb300.server import plan_with_cap_target
+
+    class Err(RuntimeError):
+        def __init__(self, code, msg):
+            super().__init__(msg)
+            self.code = code
+
+    OOM, ARG = 2, 1
+    calls = []
+
+    def make_needing(need):
+        def make(cap):
+            calls.append(cap)
+            if cap != 0 and cap < need:
+                raise Err(OOM, f"one w-plane needs {need} bytes of workspace, above the cap {cap}")
+            return ("plan", cap)
+        return make
+
+    assert plan_with_cap_target(make_needing(5), 1, 64, Err, OOM) == ("plan", 8)
+    assert calls == [1, 2, 4, 8]
+    calls.clear()
+    assert plan_with_cap_target(make_needing(18), 8, 20, Err, OOM) == ("plan", 20)   # capped at the limit
+    assert calls == [8, 16, 20]
+    calls.clear()
+    with pytest.raises(Err):                       # beyond the limit: the last cap error
+        plan_with_cap_target(make_needing(100), 8, 20, Err, OOM)
+    assert calls == [8, 16, 20]
+
+    def other(cap):
+        raise Err(ARG, "frequencies must be positive")
+    with pytest.raises(Err):
+        plan_with_cap_target(other, 8, 64, Err, OOM)
+
+    def real_oom(cap):                             # a device allocation failure is not the cap
+        raise Err(OOM, "device allocation of 123 bytes failed")
+    with pytest.raises(Err):
+        plan_with_cap_target(real_oom, 8, 64, Err, OOM)
