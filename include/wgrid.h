@@ -100,7 +100,9 @@ typedef struct wg_options {
                               1 = cuFFT 2-D, 2 = the library's double-float FFT (WG_F64 only,
                               grid sides up to 6400 with prime factors 2, 3, 5, 7, 11, and
                               sides up to 25600 that are 2 or 4 times such a side (each line
-                              then runs on 2 or 4 CTAs); its ~5e-15 rounding is amplified by the
+                              then runs on a thread-block cluster of 2 or 4 CTAs, as do lines
+                              above 2048 points whose half needs only the radices 8, 4, 5,
+                              3); its ~5e-15 rounding is amplified by the
                               1 / psi correction, so the planner may raise sigma for it; the
                               uv planes are then kept as double-float pairs and (de)gridded in
                               pair arithmetic),

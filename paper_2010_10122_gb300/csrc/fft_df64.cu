@@ -538,8 +538,8 @@ struct Df64Fft {
   float4* tw_v = nullptr;
 };
 
-// Two lines of n df64 complex values in shared memory per CTA (two CTAs per SM up to n = 3584);
-// longer lines (up to kDf64MaxSplitSide) are split over two or four CTAs.
+// Two buffers of n df64 complex values in shared memory per CTA (two CTAs per SM up to n =
+// 3584); split lines (df64_line_split) run on clusters of two or four CTAs.
 static constexpr int64_t kMaxSide = kDf64MaxSide;
 
 bool df64_fft_supported(int64_t nu, int64_t nv) { return df64_side_ok(nu) && df64_side_ok(nv); }

@@ -72,9 +72,11 @@ constexpr int kF32MaxPart = 12800;
 // sides at most 46340: a plane holds fewer than 2^31 elements (32-bit offsets within a plane)
 constexpr int kF32MaxSide = 46340;
 bool f32_side_ok(int64_t n);
-// The double-float FFT keeps two lines of n complex df64 values in shared memory per CTA
-// (200 KB): sides up to 6400 whose prime factors are 2, 3, 5, 7 and 11 run one line per CTA;
-// sides up to 25600 that are 2 or 4 times such a side run each line on 2 or 4 CTAs.
+// The double-float FFT keeps two buffers of n complex df64 values in shared memory per CTA
+// (200 KB at most): sides up to 6400 whose prime factors are 2, 3, 5, 7 and 11 run one line
+// per CTA (above 2048 points as two halves on a cluster of 2 CTAs when the half needs only the
+// radices 8, 4, 5, 3); sides up to 25600 that are 2 or 4 times such a side run each line on a
+// cluster of 2 or 4 CTAs.
 constexpr int64_t kDf64MaxSide = 6400;
 constexpr int64_t kDf64MaxSplitSide = 4 * kDf64MaxSide;
 // Radix plan and CTA size of one double-float line transform: radices 8 and 4 for the power
