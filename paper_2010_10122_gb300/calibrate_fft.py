@@ -25,22 +25,60 @@ def smooth(m, primes=(2, 3, 5, 7, 11)):
     return m == 1
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--max-n", type=int, default=16384)
-    ap.add_argument("--min-n", type=int, default=0)
-    ap.add_argument("--columns", default="c2c,z2z,df64,f32")
-    ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)),
-                                                  "csrc", "fft_table.inc"))
-    args = ap.parse_args()
-    cols = args.columns.split(",")
+COLUMNS = ("c2c", "z2z", "df64", "f32")
+# (precision, bytes per complex value, impl of wg_fft_time) per column
+KINDS = (("f32", 8, 1), ("f64", 16, 1), ("f64", 16, 2), ("f32", 8, 4))
+
+
+def read_table(path):
+    """{n: [c2c, z2z, df64, f32]} from a table file (missing columns read as 0)."""
     old = {}
-    if os.path.exists(args.out):
-        for ln in open(args.out):
+    if os.path.exists(path):
+        for ln in open(path):
             ln = ln.strip()
             if ln.startswith("{"):
                 v = [float(x) for x in ln.strip("{},").split(",")]
                 old[int(v[0])] = (v[1:] + [0.0] * 4)[:4]
+    return old
+
+
+def table_plan(old, cols, min_n, max_n):
+    """Rows of the new table in size order: (n, [column -> measure?]).  Sizes are n = 32 m, m
+    11-smooth, up to max_n, plus every size the old table has beyond it; a column is re-measured
+    only when it is selected and n lies in [min_n, max_n] (or the old table lacks n)."""
+    top = max([max_n] + list(old))
+    out = []
+    for m in range(4, top // 32 + 1):
+        if not smooth(m):
+            continue
+        n = 32 * m
+        if n > max_n and n not in old:
+            continue
+        measure = [not ((name not in cols or n < min_n or n > max_n) and n in old)
+                   for name in COLUMNS]
+        out.append((n, measure))
+    return out
+
+
+def format_table(rows, device_name):
+    lines = [f"// cuFFT batched 2-D plane transform times on {device_name}, measured by\n",
+             "// paper_2010_10122_gb300/calibrate_fft.py: {n, ms per plane C2C, ms per plane Z2Z, "
+             "ms per plane double-float, ms per plane library FP32}\n"]
+    for n, a, b, c, d in rows:
+        lines.append(f"{{{n}, {a:.6g}, {b:.6g}, {c:.6g}, {d:.6g}}},\n")
+    return "".join(lines)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--max-n", type=int, default=16384)
+    ap.add_argument("--min-n", type=int, default=0)
+    ap.add_argument("--columns", default=",".join(COLUMNS))
+    ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                                                  "csrc", "fft_table.inc"))
+    args = ap.parse_args()
+    cols = args.columns.split(",")
+    old = read_table(args.out)
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     from paper_2010_10122_gb300 import _build
     _build.build()
@@ -48,19 +86,10 @@ def main():
     import torch
     rows = []
     t0 = time.time()
-    # sizes beyond --max-n (or below --min-n) keep the existing table's entries
-    top = max([args.max_n] + list(old))
-    for m in range(4, top // 32 + 1):
-        if not smooth(m):
-            continue
-        n = 32 * m
-        if n > args.max_n and n not in old:
-            continue
+    for n, measure in table_plan(old, cols, args.min_n, args.max_n):
         out = [n]
-        for c, (prec, b, impl) in enumerate((("f32", 8, 1), ("f64", 16, 1), ("f64", 16, 2),
-                                             ("f32", 8, 4))):
-            name = ("c2c", "z2z", "df64", "f32")[c]
-            if (name not in cols or n < args.min_n or n > args.max_n) and n in old:
+        for c, (prec, b, impl) in enumerate(KINDS):
+            if not measure[c]:
                 out.append(old[n][c])
                 continue
             batch = max(1, min(64, int((1.5 * 2**30) // (n * n * b))))
@@ -72,13 +101,8 @@ def main():
         rows.append(out)
         print(f"n={n:6d} c2c {out[1]*1e3:9.2f} us/plane  z2z {out[2]*1e3:10.2f} us/plane  "
               f"df64 {out[3]*1e3:10.2f} us/plane  f32 {out[4]*1e3:10.2f} us/plane", flush=True)
-    dev = torch.cuda.get_device_name(0)
     with open(args.out, "w") as f:
-        f.write(f"// cuFFT batched 2-D plane transform times on {dev}, measured by\n")
-        f.write("// paper_2010_10122_gb300/calibrate_fft.py: {n, ms per plane C2C, ms per plane Z2Z, "
-                "ms per plane double-float, ms per plane library FP32}\n")
-        for n, a, b, c, d in rows:
-            f.write(f"{{{n}, {a:.6g}, {b:.6g}, {c:.6g}, {d:.6g}}},\n")
+        f.write(format_table(rows, torch.cuda.get_device_name(0)))
     print(f"wrote {len(rows)} sizes to {args.out} in {time.time() - t0:.0f} s")
 
 

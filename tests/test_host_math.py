@@ -269,3 +269,28 @@ def test_planner_f32_library_fft_sides(wg):
                     m //= f
             ok = ok or m == 1
         assert ok, p
+
+
+def test_calibration_table_merge(tmp_path):
+    """calibrate_fft re-measures only the selected columns in [min_n, max_n] and keeps every
+    other entry of the existing table, including sizes beyond max_n (a range-limited run once
+    dropped them)."""
+    from paper_2010_10122_gb300 import calibrate_fft as cf
+    src = open(os.path.join(os.path.dirname(__file__), "..", "paper_2010_10122_gb300", "csrc",
+                            "fft_table.inc")).read()
+    path = tmp_path / "t.inc"
+    path.write_text(src)
+    old = cf.read_table(str(path))
+    assert len(old) > 100 and all(len(v) == 4 for v in old.values())
+    plan = dict(cf.table_plan(old, ["df64"], 2049, 6400))
+    assert set(plan) == set(old)                          # no size lost or added
+    for n, measure in plan.items():
+        assert measure == [False, False, 2049 <= n <= 6400, False]
+    # a fresh table: every column of every size measured
+    fresh = cf.table_plan({}, list(cf.COLUMNS), 0, 1024)
+    assert [n for n, _ in fresh] == [32 * m for m in range(4, 33) if cf.smooth(m)]
+    assert all(all(m) for _, m in fresh)
+    # the written form reads back
+    rows = [[n] + old[n] for n in sorted(old)]
+    path.write_text(cf.format_table(rows, "GPU"))
+    assert cf.read_table(str(path)) == {n: [float(f"{x:.6g}") for x in v] for n, v in old.items()}
